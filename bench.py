@@ -1,0 +1,438 @@
+#!/usr/bin/env python
+"""FCIQMC configurations updated per second on GB300.
+
+Workload (default ``c2``): 1D periodic real-space Bose-Hubbard model, M = N =
+20, t = 1, U = 2 (39-bit addresses), FP64 amplitudes, threshold 1, target
+N_t = 1e7 walkers, dt = 1e-3, started from N_w = 10 on uniform filling.  The
+first 25 % of the configuration's 10k steps are equilibration (untimed, as the
+paper discards equilibration); then W warm-up steps and K timed steps.
+
+value   = sum over timed steps of len (occupied configurations updated) /
+          device time of the K steps (CUDA events on the run's stream,
+          graph-replayed steps), summed over ranks / max time over ranks.
+e2e     = the same metric through the public API as a user drives it: per
+          step one parameter write from pinned host memory, one step, and
+          one read of the step's statistics row back to the host.
+roofline= the dominant kernel's algorithmic bytes per launch / its mean
+          CUDA-event duration (steps launched kernel by kernel right after
+          the timed region), against the measured HBM copy bandwidth.
+cpu_baseline = the CPU oracle, single thread, on a bounded sample of the
+          equilibrated vector (rank 0, N = 1 only).
+
+--impl reference runs the CPU oracle instead (the paper ships no GPU code):
+each step is one oracle step on a bounded sample of the same workload.
+With --gpus N > 1 under torchrun every rank steps an independent replica
+(run_id = rank): the step has no data-path exchange to shard.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "FCIQMC configs updated/s"
+UNIT = "configs/s"
+MODE_CODE = {"INT": 0, "REAL64": 1, "REAL32": 2, "DETERMINISTIC": 3}
+DTYPE = {"INT": "int64", "REAL64": "f64", "REAL32": "f32", "DETERMINISTIC": "f64"}
+# bytes fq_run_stats copies back per call: the error word and the run state
+STATS_D2H_BYTES = 4 + 144
+KERNEL_FILES = ["fq_kernels.cuh", "fq_device.cuh", "fq_shared.h"]
+
+
+def describe(cfg, name):
+    kind = {1: "1D periodic real-space", 2: "2D periodic real-space", 3: "1D momentum-space"}
+    lat = "%dx%d" % (cfg["Lx"], cfg["Ly"]) if cfg["kind"] == 2 else "M=%d" % cfg["Lx"]
+    return ("%s: %s Bose-Hubbard %s, N=%d, t=%g, U=%g, %s, N_t=%.0e, dt=%g, seed %d, start 10 "
+            "walkers on the starting address" % (name, kind[cfg["kind"]], lat, cfg["N"], cfg["t"],
+                                                 cfg["u"], cfg["mode"], cfg["target"], cfg["dt"],
+                                                 cfg["seed"]))
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Dist:
+    """Barrier and max/sum over ranks (a no-op for one process)."""
+
+    def __init__(self, world, backend):
+        self.world = world
+        self.dist = None
+        if world > 1:
+            import torch.distributed as dist
+
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist:
+            self.dist.barrier()
+
+    def reduce(self, value: float, op: str) -> float:
+        if not self.dist:
+            return value
+        import torch
+
+        dev = "cuda" if self.dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([value], dtype=torch.float64, device=dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX if op == "max" else self.dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.dist:
+            self.dist.destroy_process_group()
+
+
+def aggregate(dist: Dist, elapsed_s: float, units: float):
+    """Whole-job throughput: units of all ranks over the slowest rank's time."""
+    t = dist.reduce(elapsed_s, "max")
+    u = dist.reduce(units, "sum")
+    return u / t, t
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_digest():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_FILES:
+        with open(os.path.join(ROOT, "paper_2601_19505_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_alg_byte(kernel: str, workload: str):
+    """DRAM bytes per algorithmic byte of `kernel` from a committed ncu summary
+    (profiles/<kernel>_<workload>.md), if its kernel digest is current."""
+    path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload))
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("- ") and ":" in line:
+                k, v = line[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    try:
+        if vals.get("kernel_digest") != kernel_digest():
+            return None
+        return float(vals["dram_bytes_per_launch"]) / float(vals["algorithmic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def sizes(cfg):
+    kb = 8 if cfg["N"] + cfg["Lx"] * cfg["Ly"] - 1 <= 64 else 16
+    ab = {"INT": 8, "REAL64": 8, "REAL32": 4, "DETERMINISTIC": 8}[cfg["mode"]]
+    sb = {"INT": 4, "REAL64": 8, "REAL32": 4, "DETERMINISTIC": 8}[cfg["mode"]]
+    return kb, ab, sb
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timings (baseline only)
+
+def oracle_rate(cfg, keys_int, amps, shift, step, budget_s=12.0, seed=0):
+    """Oracle configs/s on a bounded sample: one step on n entries, n grown
+    until one step takes about budget_s / 3, then timed once more."""
+    import oracle as O
+
+    m = O.Model(cfg["kind"], cfg["Lx"], cfg["Ly"], cfg["N"], cfg["t"], cfg["u"])
+    p = O.default_params(mode=MODE_CODE[cfg["mode"]], dt=cfg["dt"], target=cfg["target"],
+                         seed=cfg["seed"])
+    rng = np.random.default_rng(seed)
+    n = min(len(keys_int), 20000)
+    rate = None
+    while True:
+        idx = np.sort(rng.choice(len(keys_int), n, replace=False))
+        run = O.Run(m, p)
+        run.seed([keys_int[i] for i in idx], amps[idx], shift, step)
+        t0 = time.perf_counter()
+        run.step(1)
+        dt = time.perf_counter() - t0
+        rate = n / dt
+        if dt > budget_s / 3 or n >= len(keys_int):
+            return rate, n, dt
+        n = int(min(len(keys_int), n * max(2.0, (budget_s / 3) / dt)))
+
+
+def synthetic_vector(cfg, n, seed):
+    import oracle as O
+
+    m = O.Model(cfg["kind"], cfg["Lx"], cfg["Ly"], cfg["N"], cfg["t"], cfg["u"])
+    rng = np.random.default_rng(seed)
+    occ = W.random_occupations(cfg["kind"], cfg["Lx"], cfg["Ly"], cfg["N"], n, rng, max_moves=30)
+    keys = [m.encode(o) for o in occ]
+    amps = W.random_amplitudes(len(keys), rng, mode=cfg["mode"])
+    return keys, amps, m
+
+
+def reference_arm(args, cfg, name):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as O
+
+    O.build()
+    budget = 150.0
+    pool_n = 60000
+    keys, amps, m = synthetic_vector(cfg, pool_n, 1)
+    p = O.default_params(mode=MODE_CODE[cfg["mode"]], dt=cfg["dt"], target=cfg["target"],
+                         seed=cfg["seed"])
+    # calibrate the per-entry cost, then size each step's sample
+    run = O.Run(m, p)
+    run.seed(keys[:5000], amps[:5000], -2.0, 1000)
+    t0 = time.perf_counter()
+    run.step(1)
+    per = (time.perf_counter() - t0) / 5000
+    n = int(max(200, min(pool_n, budget / max(1, args.steps + args.warmup) / per)))
+    rng = np.random.default_rng(2)
+    tot_t, tot_n = 0.0, 0
+    for s in range(args.warmup + args.steps):
+        idx = np.sort(rng.choice(len(keys), n, replace=False))
+        run = O.Run(m, p)
+        run.seed([keys[i] for i in idx], amps[idx], -2.0, 1000 + s)
+        t0 = time.perf_counter()
+        run.step(1)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            tot_t += dt
+            tot_n += n
+    value = tot_n / tot_t
+    sample = ("each step: one oracle step on %d entries drawn from a seeded synthetic %d-entry "
+              "vector of the %s workload (random hop walks from uniform filling, "
+              "threshold-shaped amplitudes)" % (n, pool_n, name))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[cfg["mode"]], "data": "synthetic",
+            "config": {"workload": describe(cfg, name), "sample_entries_per_step": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+
+def gpu_arm(args, cfg, name):
+    import torch
+
+    import paper_2601_19505_gb300 as fq
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = Dist(world, "nccl")
+    h = fq.Hamiltonian(cfg["kind"], cfg["Lx"], cfg["Ly"], cfg["N"], cfg["t"], cfg["u"])
+    p = fq.default_params(mode=MODE_CODE[cfg["mode"]], dt=cfg["dt"], target=cfg["target"],
+                          seed=cfg["seed"], run_id=rank)
+    run = fq.Run(h, p)
+    run.seed_default(W.START_WEIGHT)
+    equil = args.equil if args.equil is not None else cfg["steps"] // 4
+    done = 0
+    while done < equil:
+        k = min(500, equil - done)
+        run.step(k)
+        run.stats()
+        done += k
+    tune_steps = 0
+    if not args.no_autotune:
+        run.autotune(2)
+        tune_steps = 3 * 8
+    run.step(args.warmup)
+    run.stats()
+    run.history()  # drain
+    stream = torch.cuda.ExternalStream(run.stream) if run.stream else torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(local)
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    run.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    dist.barrier()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    hist = run.history()
+    assert len(hist) == args.steps, (len(hist), args.steps)
+    units = float(hist["len"].sum())
+    value, tmax = aggregate(dist, elapsed, units)
+
+    # per-kernel durations right after the timed region (kernel-by-kernel launch)
+    nprof = min(200, max(20, args.steps // 10))
+    before = run.stats()
+    ms = run.profile(nprof)
+    prof = run.history()
+    kb, ab, sb = sizes(cfg)
+    L_in = np.r_[before["len"], prof["len"][:-1]].astype(float)
+    L_out = prof["len"].astype(float)
+    S = prof["n_spawns"].astype(float)
+    alg = {"spawn": float(np.mean(L_in * (kb + ab) + S * (kb + sb))),
+           "merge": float(np.mean(L_in * (kb + ab) + S * (kb + sb) + L_out * (kb + ab)))}
+    kms = {"spawn": ms[0], "merge": ms[1], "shift": ms[2]}
+    dom = "merge" if ms[1] >= ms[0] else "spawn"
+    peak, peak_kind = measured_peak()
+    achieved = alg[dom] / (kms[dom] * 1e-3) / 1e9
+    ratio = traffic_per_alg_byte("k_" + dom, name)
+    traffic = alg[dom] * ratio if ratio else None
+
+    # end to end through the public API, host buffers in the loop
+    ne2e = min(args.steps, 1000)
+    t0 = time.perf_counter()
+    e2e_units = 0
+    for _ in range(ne2e):
+        run.set_target(cfg["target"])
+        run.step(1)
+        e2e_units += run.stats()["len"]
+    e2e_t = time.perf_counter() - t0
+    e2e_value, _ = aggregate(dist, e2e_t, float(e2e_units))
+
+    out = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            keys, amps = run.export()
+            kint = [int(k["lo"]) | (int(k["hi"]) << 64) for k in keys] if kb == 16 else \
+                keys["lo"].astype(object).tolist()
+            st = run.stats()
+            rate, n, tsec = oracle_rate(cfg, kint, amps, st["shift"], st["step"])
+            cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "one single-threaded oracle step on %d entries drawn at random from "
+                             "the equilibrated GPU vector (len %d), %.1f s" % (n, len(keys), tsec)}
+        L_mean = float(hist["len"].mean())
+        S_mean = float(hist["n_spawns"].mean())
+        ws = 2 * L_mean * (kb + ab) + 2 * S_mean * (kb + sb)
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[cfg["mode"]], "data": "synthetic",
+            "config": {"workload": describe(cfg, name), "equilibration_steps": equil,
+                       "autotune_steps": tune_steps, "len_mean": L_mean,
+                       "spawns_mean": S_mean, "graph_replay": True,
+                       "l2": "working set per step %.2f GB > 129 MB L2; no flush" % (ws / 1e9),
+                       "parallelism": "replicas x%d" % world},
+            "roofline": {"bound": "hbm", "kernel": "k_" + dom, "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
+                         if peak_kind == "measured" else "fallback 6800 GB/s",
+                         "traffic": traffic,
+                         "algorithmic_bytes_per_launch": alg[dom],
+                         "kernel_ms": kms,
+                         "kernel_gbs": {k: alg[k] / (kms[k] * 1e-3) / 1e9 for k in alg}},
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8,
+                    "d2h_bytes_per_step": STATS_D2H_BYTES, "steps": ne2e},
+            "gpu_launches": 3 * args.steps,
+        }
+        print(json.dumps(out), flush=True)
+    run.close()
+    dist.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=7000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--config", choices=sorted(W.CONFIGS), default="c2")
+    ap.add_argument("--equil", type=int, default=None)
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    cfg = W.CONFIGS[args.config]
+    if args.impl == "reference":
+        return reference_arm(args, cfg, args.config)
+    return gpu_arm(args, cfg, args.config)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

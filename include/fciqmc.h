@@ -1,0 +1,211 @@
+/*
+ * fciqmc.h -- C ABI of libfciqmc: one FCIQMC time step over a sparse walker
+ * vector for Bose-Hubbard Hamiltonians, run as hand-written CUDA kernels on
+ * one GPU (sm_103a).  The method is the one of the Rimu.jl paper
+ * (arXiv 2601.19505), Secs. 3.1-3.2, 4.2, 6.1-6.3 and 7.1.
+ *
+ * Calls follow the paper's statement of a calculation (Sec. 2.1): create a
+ * Hamiltonian from its parameters, seed a walker vector, set the time step,
+ * shift and target walker number, step n times, and read the shift, norm,
+ * projected energy and occupied-configuration count.
+ *
+ * Conventions for every call:
+ *  - Return 0 (FQ_OK) on success, a negative FQ_ERR_* code otherwise;
+ *    fq_strerror() names it.  Nothing is changed when a call fails, except
+ *    where a call says otherwise.
+ *  - Handles (fq_ham, fq_run, fq_batch) are opaque, owned by the library and
+ *    released by the matching *_destroy call.  A fq_ham must outlive every
+ *    run created from it; runs must outlive every batch that holds them.
+ *  - Input arrays are owned by the caller and copied before the call returns.
+ *    Outputs are written into caller buffers whose capacity is passed in.
+ *  - All pointers in this header are HOST pointers.  Device memory is owned
+ *    by the library; it comes from the caller's allocator when one is given
+ *    (e.g. PyTorch's caching allocator), else from cudaMallocAsync.
+ *  - There is no CPU fallback: without a usable CUDA device, fq_run_create
+ *    returns FQ_ERR_CUDA.
+ *  - Stepping is asynchronous on the run's CUDA stream.  Errors that arise on
+ *    the device (a full buffer, a dead population) are reported by the next
+ *    call that synchronises (fq_run_sync, _stats, _history, _export); the
+ *    run is then left at its last completed step ("rolled back").
+ *  - Not thread-safe per handle: one host thread at a time per run or batch.
+ */
+#ifndef FCIQMC_H
+#define FCIQMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fq_ham fq_ham;
+typedef struct fq_run fq_run;
+typedef struct fq_batch fq_batch;
+
+/* A Fock address (Sec. 6.1): the occupation bit string of N + M - 1 bits, n_m
+ * one-bits for mode m and one zero-bit between consecutive modes, mode 1 in
+ * the least significant bit of lo; bits 64..127 in hi (0 when N+M-1 <= 64).
+ * Example: BoseFS(0,2,3,4,0,1) is lo = 0b100111101110110 = 20342, hi = 0. */
+typedef struct { uint64_t lo, hi; } fq_key;
+
+/* Hamiltonians (Eq. bose-hubbard-hamiltonian and its momentum-space form,
+ * Sec. 6.3).  REAL_1D: periodic ring of Lx >= 3 sites (Ly = 1).  REAL_2D:
+ * periodic Lx x Ly lattice, Lx, Ly >= 3, site x + Lx*y.  MOM_1D: Lx momentum
+ * modes (Ly = 1, 2 <= Lx <= 64), mode j carries k = 2 pi (j - floor(Lx/2))/Lx. */
+enum { FQ_BH_REAL_1D = 1, FQ_BH_REAL_2D = 2, FQ_BH_MOM_1D = 3 };
+
+/* Walker representation.  INT: integer walkers (int64 amplitudes, the
+ * original integer-coefficient formulation).  REAL64: FP64 amplitudes with
+ * matrix and vector compression (Sec. 3.2).  REAL32: amplitudes and spawns
+ * stored in FP32, every sum and estimator in FP64.  DETERMINISTIC: no
+ * compression at all, the power iteration of Eq. fciqmc (FP64). */
+enum { FQ_MODE_INT = 0, FQ_MODE_REAL64 = 1, FQ_MODE_REAL32 = 2, FQ_MODE_DETERMINISTIC = 3 };
+
+/* Annihilation strategy.  HASH: spawns are scattered into hash-segmented
+ * buckets and summed per address in an on-chip open-addressing table.  AUTO
+ * picks HASH (the only one built). */
+enum { FQ_ANN_AUTO = 0, FQ_ANN_HASH = 2 };
+
+enum {
+    FQ_OK = 0,
+    FQ_ERR_INVALID = -1,  /* bad argument or handle state                        */
+    FQ_ERR_NOMEM = -2,    /* device allocation failed                            */
+    FQ_ERR_CAPACITY = -3, /* spawn, vector or table capacity exceeded; rolled back */
+    FQ_ERR_TIMEOUT = -4,  /* a bounded device-side wait expired; rolled back      */
+    FQ_ERR_EMPTY = -5,    /* the population died (norm 0); rolled back            */
+    FQ_ERR_CUDA = -6      /* a CUDA runtime error, or no usable device           */
+};
+
+/* Run parameters.  dt: time step (Eq. discretised).  target: target one-norm
+ * N_t (Eq. shift-update).  zeta, xi: shift damping and forcing (Eq.
+ * shift-update).  threshold: vector-compression threshold theta (Eq.
+ * vec-compression with 1 -> theta).  t_rel: semistochastic threshold; a column
+ * is spawned exactly when |c_i| t_rel >= m_i (Sec. 7.1).  mode: FQ_MODE_*.
+ * annihilation: FQ_ANN_*.  seed, run_id: key of the counter-based random
+ * draws.  capacity_vec, capacity_spawn: maximum occupied entries of the
+ * vector and spawn entries per step (0 = derived from target and threshold). */
+typedef struct {
+    double dt, target, zeta, xi, threshold, t_rel;
+    int32_t mode, annihilation;
+    uint64_t seed;
+    uint32_t run_id, reserved;
+    size_t capacity_vec, capacity_spawn;
+} fq_params;
+
+/* One row of the time series (Sec. 4): the step number, occupied
+ * configurations (len), exact and stochastic columns spawned, spawn entries
+ * written, and after the step the shift S, the one-norm ||c||_1 and the
+ * projected-energy numerator y^T H c (hproj) and denominator y^T c (vproj). */
+typedef struct {
+    int64_t step, len, exact_steps, inexact_steps, n_spawns;
+    double shift, norm, hproj, vproj;
+} fq_stats;
+
+/* Device-memory allocator used by a run instead of cudaMallocAsync.  alloc
+ * returns a device pointer of at least `bytes` (NULL on failure) usable on
+ * `stream`; free releases it.  Both are called from the host thread that
+ * calls into the library. */
+typedef struct {
+    void *ctx;
+    void *(*alloc)(void *ctx, size_t bytes, void *stream);
+    void (*free)(void *ctx, void *ptr, size_t bytes, void *stream);
+} fq_allocator;
+
+const char *fq_version(void);
+const char *fq_strerror(int code);
+
+/* Defaults recovered from the paper's printed time series (Secs. 2.1, 4):
+ * dt = 0.01, zeta = 0.08, xi = zeta^2/4, threshold = 1, t_rel = 1,
+ * target = 1000, mode REAL64, seed 1, run_id 0, capacities derived. */
+int fq_params_default(fq_params *p);
+
+/* Create a Bose-Hubbard Hamiltonian with N bosons, hopping t, interaction u.
+ * N >= 1, N + M - 1 <= 128.  FQ_ERR_INVALID for any other shape. */
+int fq_ham_create(fq_ham **out, int kind, int Lx, int Ly, int N, double t, double u);
+void fq_ham_destroy(fq_ham *h);
+/* Number of modes M, address bits N + M - 1, and 64-bit words per address. */
+int fq_ham_info(const fq_ham *h, int *M, int *nbits, int *key_words);
+/* Fock-space dimension C(N + M - 1, N) (Sec. 2), as a double. */
+int fq_ham_dimension(const fq_ham *h, double *dim);
+/* Starting address: near-uniform filling in real space (floor(N/M) per
+ * site, the first N mod M sites one more), all bosons in k = 0 in momentum
+ * space. */
+int fq_ham_starting_address(const fq_ham *h, fq_key *out);
+/* Address <-> occupation numbers occ[0..M-1] (Sec. 6.1).  encode fails if
+ * sum(occ) != N; decode fails if the key is not a valid address. */
+int fq_encode(const fq_ham *h, const uint8_t *occ, fq_key *out);
+int fq_decode(const fq_ham *h, fq_key key, uint8_t *occ);
+/* The column of H at `key` (Sec. 6.2, operator_column), evaluated by the
+ * device code the step uses: diagonal element and the m off-diagonal
+ * entries in enumeration order (dest[k], val[k], k < min(m, cap)).  Runs on
+ * the legacy default stream and synchronises. */
+int fq_ham_column(const fq_ham *h, fq_key key, double *diag, fq_key *dest, double *val,
+                  size_t cap, size_t *m);
+
+/* Create a run: device buffers sized from the parameters, all on `stream`
+ * (a cudaStream_t; NULL = legacy default stream).  `alloc` may be NULL. */
+int fq_run_create(fq_run **out, const fq_ham *h, const fq_params *p, void *stream,
+                  const fq_allocator *alloc);
+void fq_run_destroy(fq_run *r);
+/* Replace the walker vector by n distinct (key, amplitude) pairs; zero
+ * amplitudes are dropped.  INT runs need integral amplitudes; REAL32 runs
+ * round them to FP32.  Also sets the shift S and the step counter, clears
+ * the history, and takes the norm N^(0) = sum |c|.  FQ_ERR_INVALID on a
+ * duplicate or invalid key, FQ_ERR_CAPACITY if a segment overflows. */
+int fq_run_seed(fq_run *r, const fq_key *keys, const double *amps, size_t n, double shift,
+                int64_t step);
+/* The paper's default start (Secs. 2.1, 4.2): `weight` (N_w = 10) on the
+ * starting address, shift = its diagonal element, step 0, and projected-
+ * energy reference y = N_w e_start. */
+int fq_run_seed_default(fq_run *r, double weight);
+/* Reference vector y of the projected energy (Eq. ProjectedEnergy): n <= 64
+ * distinct addresses with coefficients y.  hproj = y^T H c, vproj = y^T c. */
+int fq_run_set_reference(fq_run *r, const fq_key *keys, const double *y, size_t n);
+/* Change dt, the current shift, or the target norm before the next step. */
+int fq_run_set_dt(fq_run *r, double dt);
+int fq_run_set_shift(fq_run *r, double shift);
+int fq_run_set_target(fq_run *r, double target);
+/* Enqueue n steps c^(n+1) = Pi[1 + dt (S^(n) - H~)] c^(n) with the shift
+ * update after each (Eq. stochasticTransitionOperator, Eq. shift-update).
+ * Asynchronous; captured once into a CUDA graph and replayed. */
+int fq_run_step(fq_run *r, int64_t n);
+/* Wait for queued work; report a device-side error (the run is rolled back
+ * to its last completed step and can continue). */
+int fq_run_sync(fq_run *r);
+/* Synchronise and return the row of the last completed step (step 0 after
+ * seeding: len, shift and norm set, the rest 0). */
+int fq_run_stats(fq_run *r, fq_stats *out);
+/* Synchronise and move out the rows recorded since the last call (oldest
+ * first, at most cap; *n = rows written).  The ring holds 65536 rows; older
+ * rows are dropped. */
+int fq_run_history(fq_run *r, fq_stats *out, size_t cap, size_t *n);
+/* Synchronise and copy the walker vector, sorted by address, into caller
+ * buffers (*n = occupied entries; min(*n, cap) written). */
+int fq_run_export(fq_run *r, fq_key *keys, double *amps, size_t cap, size_t *n);
+/* Kernel-level check: run only the spawning stage of the next step on the
+ * current vector and copy out the spawn entries (destination, value; order
+ * unspecified, *n = count).  The run's state does not change. */
+int fq_run_spawns(fq_run *r, fq_key *dest, double *val, size_t cap, size_t *n);
+/* Time the launch shapes on the current vector and keep the fastest.  Each
+ * candidate runs `steps` real steps, so the run advances. */
+int fq_run_autotune(fq_run *r, int steps);
+/* Measurement: run n steps launched one kernel at a time (not from the graph)
+ * with CUDA events around each kernel on the run's stream; ms[0], ms[1],
+ * ms[2] = mean milliseconds per step of the spawning, merge and shift
+ * kernels.  The run advances n steps (n <= 4096); synchronises. */
+int fq_run_profile(fq_run *r, int n, float *ms);
+
+/* A batch: B runs (same Hamiltonian kind, address width and mode; any sizes
+ * and parameters) stepped together by one launch per kernel per step. */
+int fq_batch_create(fq_batch **out, fq_run *const *runs, int B);
+void fq_batch_destroy(fq_batch *b);
+int fq_batch_step(fq_batch *b, int64_t n);
+int fq_batch_sync(fq_batch *b);
+int fq_batch_autotune(fq_batch *b, int steps);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FCIQMC_H */

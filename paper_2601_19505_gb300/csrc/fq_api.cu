@@ -1,0 +1,1194 @@
+// fq_api.cu -- host side of libfciqmc: the C ABI declared in fciqmc.h.
+//
+// A run owns its device buffers (hash-segmented walker vector, double
+// buffered; spawn buckets; per-segment partial sums; state and history ring)
+// and a one-run batch.  A batch owns a device table of run descriptors, the
+// segment -> run map and CUDA graphs of 1 and 16 steps; each step is three
+// launches whatever the number of runs (k_spawn, k_merge, k_shift).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/fciqmc.h"
+#include "fq_kernels.cuh"
+#include "fq_launch.h"
+#include "fq_shared.h"
+
+using namespace fq;
+
+// ---------------------------------------------------------------------------
+// kernel table
+
+namespace fq {
+void register_k64_int(KernelSet*);
+void register_k64_f64(KernelSet*);
+void register_k64_f32(KernelSet*);
+void register_k128_int(KernelSet*);
+void register_k128_f64(KernelSet*);
+void register_k128_f32(KernelSet*);
+
+static KernelSet g_sets[2][3][3];
+static std::once_flag g_sets_once;
+
+const KernelSet* kernel_set(int kw, int amp, int kind) {
+    std::call_once(g_sets_once, [] {
+        register_k64_int(g_sets[0][FQ_AMP_INT]);
+        register_k64_f64(g_sets[0][FQ_AMP_F64]);
+        register_k64_f32(g_sets[0][FQ_AMP_F32]);
+        register_k128_int(g_sets[1][FQ_AMP_INT]);
+        register_k128_f64(g_sets[1][FQ_AMP_F64]);
+        register_k128_f32(g_sets[1][FQ_AMP_F32]);
+    });
+    if (kw < 1 || kw > 2 || amp < 0 || amp > 2 || kind < 1 || kind > 3) return nullptr;
+    return &g_sets[kw - 1][amp][kind - 1];
+}
+
+void launch_shift(const RunDesc* runs, int nruns, cudaStream_t s) {
+    k_shift<256><<<nruns, 256, 0, s>>>(runs);
+}
+}  // namespace fq
+
+// ---------------------------------------------------------------------------
+// handles
+
+struct fq_ham {
+    ModelParams mp;
+    int kw;  // 64-bit words per address
+};
+
+struct Alloc {
+    void* p;
+    size_t bytes;
+};
+
+struct fq_run {
+    fq_ham ham;
+    fq_params prm;
+    cudaStream_t stream;
+    fq_allocator alloc;
+    bool has_alloc;
+    int amp, det;
+    const KernelSet* ks;
+    int log2B;
+    unsigned B, Cv, Cs, slots;
+    RunState* st;
+    StatsRow* hist;
+    unsigned* vcount[2];
+    void* vkeys[2];
+    void* vamps[2];
+    void* skeys;
+    void* samps;
+    unsigned* sfill;
+    double *part_norm, *part_h, *part_v;
+    unsigned long long* part_len;
+    void* ref_keys;
+    double *ref_h, *ref_v;
+    unsigned* ref_off;
+    size_t ref_cap;
+    unsigned long long hist_read;
+    bool seeded;
+    std::vector<Alloc> allocs;
+    fq_batch* single;
+    LaunchCfg tuned;
+    bool has_tuned;
+    unsigned gen;  // bumped whenever a device pointer of the run changes
+    double* pinned;        // host staging slot for parameter updates
+    cudaEvent_t staged;    // completes when the staged value has been copied
+};
+
+struct fq_batch {
+    std::vector<fq_run*> runs;
+    const KernelSet* ks;
+    cudaStream_t stream;
+    RunDesc* d_desc;
+    unsigned* d_seg_run;
+    unsigned G;
+    LaunchCfg cfg;
+    cudaGraphExec_t g1, g16;
+    bool owned_by_run;
+    std::vector<unsigned> gens;  // run generations the descriptors were built from
+};
+
+// ---------------------------------------------------------------------------
+// small helpers
+
+static int cuda_err(cudaError_t e) {
+    if (e == cudaSuccess) return FQ_OK;
+    if (e == cudaErrorMemoryAllocation) return FQ_ERR_NOMEM;
+    return FQ_ERR_CUDA;
+}
+#define CK(x)                                      \
+    do {                                           \
+        cudaError_t _e = (x);                      \
+        if (_e != cudaSuccess) return cuda_err(_e); \
+    } while (0)
+
+static void* dev_alloc(fq_run* r, size_t bytes) {
+    if (!bytes) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (r->has_alloc) {
+        p = r->alloc.alloc(r->alloc.ctx, bytes, (void*)r->stream);
+    } else if (cudaMallocAsync(&p, bytes, r->stream) != cudaSuccess) {
+        p = nullptr;
+    }
+    if (p) r->allocs.push_back({p, bytes});
+    return p;
+}
+
+static void dev_free_all(fq_run* r) {
+    for (auto& a : r->allocs) {
+        if (r->has_alloc) r->alloc.free(r->alloc.ctx, a.p, a.bytes, (void*)r->stream);
+        else cudaFreeAsync(a.p, r->stream);
+    }
+    r->allocs.clear();
+}
+
+static unsigned next_pow2(unsigned long long x) {
+    unsigned p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+static int ilog2(unsigned x) {
+    int l = 0;
+    while ((1u << l) < x) ++l;
+    return l;
+}
+
+static int num_sms() {
+    static int n = -1;
+    if (n < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n = 1;
+    }
+    return n;
+}
+
+// ---------------------------------------------------------------------------
+// host-side address codec (Sec. 6.1)
+
+static bool key_bit(const fq_key& k, int p) { return p < 64 ? (k.lo >> p) & 1u : (k.hi >> (p - 64)) & 1u; }
+static void key_set(fq_key& k, int p) {
+    if (p < 64) k.lo |= 1ull << p; else k.hi |= 1ull << (p - 64);
+}
+static bool key_less(const fq_key& a, const fq_key& b) { return a.hi != b.hi ? a.hi < b.hi : a.lo < b.lo; }
+static bool key_same(const fq_key& a, const fq_key& b) { return a.hi == b.hi && a.lo == b.lo; }
+
+static bool key_valid(const fq_ham* h, const fq_key& k) {
+    int ones = 0;
+    for (int p = 0; p < 128; ++p)
+        if (key_bit(k, p)) {
+            if (p >= h->mp.nbits) return false;
+            ++ones;
+        }
+    return ones == h->mp.N;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI: misc
+
+extern "C" const char* fq_version(void) { return "fciqmc-gb300 0.1 (sm_103a)"; }
+
+extern "C" const char* fq_strerror(int code) {
+    switch (code) {
+    case FQ_OK: return "ok";
+    case FQ_ERR_INVALID: return "invalid argument";
+    case FQ_ERR_NOMEM: return "device allocation failed";
+    case FQ_ERR_CAPACITY: return "capacity exceeded (step rolled back)";
+    case FQ_ERR_TIMEOUT: return "device wait timed out (step rolled back)";
+    case FQ_ERR_EMPTY: return "population died (step rolled back)";
+    case FQ_ERR_CUDA: return "CUDA error or no usable device";
+    default: return "unknown error";
+    }
+}
+
+extern "C" int fq_params_default(fq_params* p) {
+    if (!p) return FQ_ERR_INVALID;
+    memset(p, 0, sizeof *p);
+    p->dt = 0.01;
+    p->target = 1000.0;
+    p->zeta = 0.08;
+    p->xi = 0.08 * 0.08 / 4.0;
+    p->threshold = 1.0;
+    p->t_rel = 1.0;
+    p->mode = FQ_MODE_REAL64;
+    p->annihilation = FQ_ANN_AUTO;
+    p->seed = 1;
+    p->run_id = 0;
+    return FQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI: Hamiltonians
+
+extern "C" int fq_ham_create(fq_ham** out, int kind, int Lx, int Ly, int N, double t, double u) {
+    if (!out) return FQ_ERR_INVALID;
+    *out = nullptr;
+    if (N < 1 || N > 255) return FQ_ERR_INVALID;
+    int M;
+    if (kind == FQ_BH_REAL_2D) {
+        if (Lx < 3 || Ly < 3) return FQ_ERR_INVALID;
+        M = Lx * Ly;
+    } else if (kind == FQ_BH_REAL_1D) {
+        if (Lx < 3 || Ly != 1) return FQ_ERR_INVALID;
+        M = Lx;
+    } else if (kind == FQ_BH_MOM_1D) {
+        if (Lx < 2 || Lx > FQ_MAX_MOM_MODES || Ly != 1) return FQ_ERR_INVALID;
+        M = Lx;
+    } else {
+        return FQ_ERR_INVALID;
+    }
+    if (N + M - 1 > 128 || !std::isfinite(t) || !std::isfinite(u)) return FQ_ERR_INVALID;
+    fq_ham* h = new (std::nothrow) fq_ham;
+    if (!h) return FQ_ERR_NOMEM;
+    memset(h, 0, sizeof *h);
+    ModelParams& mp = h->mp;
+    mp.kind = kind; mp.M = M; mp.N = N; mp.Lx = Lx; mp.Ly = Ly; mp.nbits = N + M - 1;
+    mp.t = t; mp.u = u;
+    mp.g = u / (double)(2 * M);
+    if (kind == FQ_BH_MOM_1D) {
+        // mode j (1-based) carries k_j = 2 pi (j - floor(M/2)) / M
+        for (int m = 0; m < M; ++m) {
+            double k = (2.0 * M_PI * (double)(m + 1 - M / 2)) / (double)M;
+            mp.eps[m] = (-2.0 * t) * cos(k);
+        }
+    }
+    h->kw = mp.nbits <= 64 ? 1 : 2;
+    *out = h;
+    return FQ_OK;
+}
+
+extern "C" void fq_ham_destroy(fq_ham* h) { delete h; }
+
+extern "C" int fq_ham_info(const fq_ham* h, int* M, int* nbits, int* key_words) {
+    if (!h) return FQ_ERR_INVALID;
+    if (M) *M = h->mp.M;
+    if (nbits) *nbits = h->mp.nbits;
+    if (key_words) *key_words = h->kw;
+    return FQ_OK;
+}
+
+extern "C" int fq_ham_dimension(const fq_ham* h, double* dim) {
+    if (!h || !dim) return FQ_ERR_INVALID;
+    // C(N + M - 1, N): exact in 128-bit integers while it fits, else FP64
+    unsigned __int128 c = 1;
+    bool exact = true;
+    for (int i = 1; i <= h->mp.N && exact; ++i) {
+        const unsigned __int128 f = (unsigned __int128)(h->mp.M - 1 + i);
+        if (c > (~(unsigned __int128)0) / f) exact = false;
+        else c = c * f / (unsigned __int128)i;
+    }
+    if (exact) {
+        *dim = (double)c;
+    } else {
+        double d = 1.0;
+        for (int i = 1; i <= h->mp.N; ++i) d = d * (double)(h->mp.M - 1 + i) / (double)i;
+        *dim = d;
+    }
+    return FQ_OK;
+}
+
+extern "C" int fq_encode(const fq_ham* h, const uint8_t* occ, fq_key* out) {
+    if (!h || !occ || !out) return FQ_ERR_INVALID;
+    int s = 0;
+    for (int m = 0; m < h->mp.M; ++m) s += occ[m];
+    if (s != h->mp.N) return FQ_ERR_INVALID;
+    fq_key k = {0, 0};
+    int pos = 0;
+    for (int m = 0; m < h->mp.M; ++m) {
+        for (int j = 0; j < occ[m]; ++j) key_set(k, pos++);
+        if (m < h->mp.M - 1) ++pos;
+    }
+    *out = k;
+    return FQ_OK;
+}
+
+extern "C" int fq_decode(const fq_ham* h, fq_key key, uint8_t* occ) {
+    if (!h || !occ || !key_valid(h, key)) return FQ_ERR_INVALID;
+    memset(occ, 0, (size_t)h->mp.M);
+    int m = 0;
+    for (int p = 0; p < h->mp.nbits; ++p) {
+        if (key_bit(key, p)) occ[m]++;
+        else ++m;
+    }
+    return FQ_OK;
+}
+
+extern "C" int fq_ham_starting_address(const fq_ham* h, fq_key* out) {
+    if (!h || !out) return FQ_ERR_INVALID;
+    std::vector<uint8_t> occ((size_t)h->mp.M, 0);
+    if (h->mp.kind == FQ_BH_MOM_1D) {
+        occ[(size_t)(h->mp.M / 2 - 1)] = (uint8_t)h->mp.N;
+    } else {
+        for (int m = 0; m < h->mp.M; ++m)
+            occ[(size_t)m] = (uint8_t)(h->mp.N / h->mp.M + (m < h->mp.N % h->mp.M ? 1 : 0));
+    }
+    return fq_encode(h, occ.data(), out);
+}
+
+static int ham_column_dev(const fq_ham* h, int amp, fq_key key, double* diag, fq_key* dest,
+                          double* val, size_t cap, size_t* m_out, cudaStream_t s) {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return FQ_ERR_CUDA;
+    const KernelSet* ks = kernel_set(h->kw, amp, h->mp.kind);
+    const size_t kb = ks->key_bytes;
+    const unsigned ccap = (unsigned)std::min<size_t>(cap, 1u << 20);
+    void* d_key = nullptr;
+    void* d_dest = nullptr;
+    double *d_val = nullptr, *d_diag = nullptr;
+    unsigned* d_m = nullptr;
+    CK(cudaMalloc(&d_key, kb));
+    CK(cudaMalloc(&d_dest, kb * (ccap ? ccap : 1)));
+    CK(cudaMalloc(&d_val, sizeof(double) * (ccap ? ccap : 1)));
+    CK(cudaMalloc(&d_diag, sizeof(double)));
+    CK(cudaMalloc(&d_m, sizeof(unsigned)));
+    unsigned char kbuf[16];
+    memcpy(kbuf, &key, 16);
+    ks->column(h->mp, kbuf, d_dest, d_val, ccap, d_diag, d_m, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    unsigned m = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&m, d_m, sizeof m, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && diag) e = cudaMemcpy(diag, d_diag, sizeof(double), cudaMemcpyDeviceToHost);
+    const size_t nw = std::min<size_t>(m, ccap);
+    if (e == cudaSuccess && nw && val) e = cudaMemcpy(val, d_val, sizeof(double) * nw, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && nw && dest) {
+        std::vector<unsigned char> tmp(kb * nw);
+        e = cudaMemcpy(tmp.data(), d_dest, kb * nw, cudaMemcpyDeviceToHost);
+        for (size_t i = 0; i < nw; ++i) {
+            fq_key k = {0, 0};
+            memcpy(&k, tmp.data() + i * kb, kb);
+            dest[i] = k;
+        }
+    }
+    cudaFree(d_key); cudaFree(d_dest); cudaFree(d_val); cudaFree(d_diag); cudaFree(d_m);
+    if (m_out) *m_out = m;
+    return cuda_err(e);
+}
+
+extern "C" int fq_ham_column(const fq_ham* h, fq_key key, double* diag, fq_key* dest, double* val,
+                             size_t cap, size_t* m) {
+    if (!h || !key_valid(h, key)) return FQ_ERR_INVALID;
+    return ham_column_dev(h, FQ_AMP_F64, key, diag, dest, val, cap, m, 0);
+}
+
+// ---------------------------------------------------------------------------
+// runs: sizing and creation
+
+static size_t max_offdiag(const ModelParams& mp) {
+    const size_t nocc = (size_t)std::min(mp.N, mp.M);
+    if (mp.kind == FQ_BH_REAL_1D) return 2 * nocc;
+    if (mp.kind == FQ_BH_REAL_2D) return 4 * nocc;
+    return (nocc * (nocc + 1) / 2) * (size_t)(mp.M / 2 + 1);
+}
+
+static void fill_desc(const fq_run* r, RunDesc& d, unsigned seg_base) {
+    memset(&d, 0, sizeof d);
+    d.mp = r->ham.mp;
+    d.mode_det = r->det;
+    d.theta = r->prm.threshold;
+    d.t_rel = r->prm.t_rel;
+    d.key_x = (unsigned)r->prm.seed;
+    d.key_y = (unsigned)(r->prm.seed >> 32) ^ (unsigned)(r->prm.run_id * 0x9E3779B9u);
+    d.log2B = r->log2B;
+    d.B = r->B;
+    d.seg_base = seg_base;
+    d.Cv = r->Cv;
+    d.Cs = r->Cs;
+    for (int i = 0; i < 2; ++i) {
+        d.vkeys[i] = r->vkeys[i];
+        d.vamps[i] = r->vamps[i];
+        d.vcount[i] = r->vcount[i];
+    }
+    d.skeys = r->skeys;
+    d.samps = r->samps;
+    d.sfill = r->sfill;
+    d.st = r->st;
+    d.hist = r->hist;
+    d.ref_keys = r->ref_keys;
+    d.ref_h = r->ref_h;
+    d.ref_v = r->ref_v;
+    d.ref_off = r->ref_off;
+    d.part_norm = r->part_norm;
+    d.part_h = r->part_h;
+    d.part_v = r->part_v;
+    d.part_len = r->part_len;
+}
+
+static LaunchCfg default_cfg(const KernelSet* ks, unsigned slots, unsigned G) {
+    LaunchCfg c;
+    c.spawn_block = 256;
+    c.merge_block = 512;
+    c.slots = slots;
+    const int sms = num_sms();
+    int occ_s = ks->spawn_occupancy(c.spawn_block);
+    const size_t smem = (size_t)slots * (ks->key_bytes + ks->acc_bytes);
+    int occ_m = ks->merge_occupancy(c.merge_block, smem);
+    if (occ_s < 1) occ_s = 1;
+    if (occ_m < 1) occ_m = 1;
+    c.spawn_grid = (int)std::min<long long>((long long)sms * occ_s, G);
+    c.merge_grid = (int)std::min<long long>((long long)sms * occ_m, G);
+    if (c.spawn_grid < 1) c.spawn_grid = 1;
+    if (c.merge_grid < 1) c.merge_grid = 1;
+    return c;
+}
+
+static void batch_free(fq_batch* b);
+static int batch_build(fq_batch* b);
+
+extern "C" int fq_run_create(fq_run** out, const fq_ham* h, const fq_params* p, void* stream,
+                             const fq_allocator* alloc) {
+    if (!out || !h || !p) return FQ_ERR_INVALID;
+    *out = nullptr;
+    if (!(p->dt > 0) || !(p->target > 0) || !(p->zeta >= 0) || !(p->xi >= 0) || !(p->t_rel > 0))
+        return FQ_ERR_INVALID;
+    if (p->mode < FQ_MODE_INT || p->mode > FQ_MODE_DETERMINISTIC) return FQ_ERR_INVALID;
+    if (p->mode != FQ_MODE_DETERMINISTIC && p->mode != FQ_MODE_INT && !(p->threshold > 0))
+        return FQ_ERR_INVALID;
+    if (p->annihilation != FQ_ANN_AUTO && p->annihilation != FQ_ANN_HASH) return FQ_ERR_INVALID;
+    if (p->mode == FQ_MODE_INT && p->target > 1e12) return FQ_ERR_INVALID;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return FQ_ERR_CUDA;
+
+    fq_run* r = new (std::nothrow) fq_run();
+    if (!r) return FQ_ERR_NOMEM;
+    r->ham = *h;
+    r->prm = *p;
+    r->stream = (cudaStream_t)stream;
+    r->has_alloc = alloc && alloc->alloc && alloc->free;
+    if (r->has_alloc) r->alloc = *alloc;
+    r->amp = p->mode == FQ_MODE_INT ? FQ_AMP_INT : p->mode == FQ_MODE_REAL32 ? FQ_AMP_F32 : FQ_AMP_F64;
+    r->det = p->mode == FQ_MODE_DETERMINISTIC;
+    r->ks = kernel_set(h->kw, r->amp, h->mp.kind);
+
+    // capacities: after compression every entry has |c| >= threshold, so
+    // len <= norm / threshold; spawns per step <= norm * max(1, t_rel) + len
+    double dim = 0;
+    fq_ham_dimension(h, &dim);
+    const double th = r->det ? 1.0 : (p->mode == FQ_MODE_INT ? 1.0 : std::min(1.0, p->threshold));
+    double lcap = p->capacity_vec ? (double)p->capacity_vec : 2.0 * p->target / th + 1024.0;
+    if (r->det && !p->capacity_vec) lcap = std::min(dim * 1.05 + 1024.0, 1.0e9);
+    lcap = std::min(lcap, dim * 1.05 + 1024.0);
+    double scap = p->capacity_spawn ? (double)p->capacity_spawn
+                                    : 1.5 * lcap * std::max(1.0, p->t_rel) + 4096.0;
+    if (r->det && !p->capacity_spawn) scap = lcap * (double)max_offdiag(h->mp) + 4096.0;
+    if (lcap > 4.0e9 || scap > 8.0e9) {
+        delete r;
+        return FQ_ERR_INVALID;
+    }
+    const size_t kb = r->ks->key_bytes, ab = r->ks->amp_bytes, sb = r->ks->spawn_bytes,
+                 cb = r->ks->acc_bytes;
+    const unsigned max_slots = 8192;
+    double per_seg = 3000.0;
+    for (;;) {
+        const unsigned long long want = (unsigned long long)std::ceil((lcap + scap) / per_seg);
+        r->B = next_pow2(std::max<unsigned long long>(1, want));
+        const double mv = lcap / r->B, ms = scap / r->B;
+        r->Cv = (unsigned)((mv + 5.0 * std::sqrt(mv) + 32.0 + 31.0) / 32.0) * 32u;
+        r->Cs = (unsigned)((ms + 5.0 * std::sqrt(ms) + 32.0 + 31.0) / 32.0) * 32u;
+        r->slots = std::max(512u, next_pow2((unsigned long long)std::ceil(1.15 * (r->Cv + r->Cs))));
+        if (r->slots <= max_slots) break;
+        per_seg *= 0.75;
+    }
+    r->log2B = ilog2(r->B);
+    const unsigned B = r->B;
+
+    bool ok = true;
+    auto A = [&](size_t bytes) {
+        void* q = dev_alloc(r, bytes);
+        if (!q) ok = false;
+        return q;
+    };
+    r->st = (RunState*)A(sizeof(RunState));
+    r->hist = (StatsRow*)A(sizeof(StatsRow) * FQ_HIST_CAP);
+    for (int i = 0; i < 2; ++i) {
+        r->vcount[i] = (unsigned*)A(sizeof(unsigned) * B);
+        r->vkeys[i] = A(kb * (size_t)B * r->Cv);
+        r->vamps[i] = A(ab * (size_t)B * r->Cv);
+    }
+    r->skeys = A(kb * (size_t)B * r->Cs);
+    r->samps = A(sb * (size_t)B * r->Cs);
+    r->sfill = (unsigned*)A(sizeof(unsigned) * B);
+    r->part_norm = (double*)A(sizeof(double) * B);
+    r->part_h = (double*)A(sizeof(double) * B);
+    r->part_v = (double*)A(sizeof(double) * B);
+    r->part_len = (unsigned long long*)A(sizeof(unsigned long long) * B);
+    r->ref_off = (unsigned*)A(sizeof(unsigned) * (B + 1));
+    r->ref_cap = 0;
+    r->ref_keys = nullptr;
+    r->ref_h = r->ref_v = nullptr;
+    if (!ok) {
+        dev_free_all(r);
+        cudaStreamSynchronize(r->stream);
+        delete r;
+        return FQ_ERR_NOMEM;
+    }
+    (void)cb;
+    RunState s0;
+    memset(&s0, 0, sizeof s0);
+    s0.dt = p->dt;
+    s0.target = p->target;
+    s0.zeta = p->zeta;
+    s0.xi = p->xi;
+    s0.norm = 1.0;
+    cudaError_t e = cudaMemcpyAsync(r->st, &s0, sizeof s0, cudaMemcpyHostToDevice, r->stream);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        e = cudaMemsetAsync(r->vcount[i], 0, sizeof(unsigned) * B, r->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->sfill, 0, sizeof(unsigned) * B, r->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->ref_off, 0, sizeof(unsigned) * (B + 1), r->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+    if (e != cudaSuccess) {
+        dev_free_all(r);
+        delete r;
+        return cuda_err(e);
+    }
+    r->seeded = false;
+    r->hist_read = 0;
+    r->single = nullptr;
+    r->has_tuned = false;
+    r->gen = 0;
+    if (cudaMallocHost((void**)&r->pinned, sizeof(double)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&r->staged, cudaEventDisableTiming) != cudaSuccess) {
+        dev_free_all(r);
+        cudaStreamSynchronize(r->stream);
+        delete r;
+        return FQ_ERR_NOMEM;
+    }
+    cudaEventRecord(r->staged, r->stream);
+    *out = r;
+    return FQ_OK;
+}
+
+extern "C" void fq_run_destroy(fq_run* r) {
+    if (!r) return;
+    cudaStreamSynchronize(r->stream);
+    if (r->single) batch_free(r->single);
+    dev_free_all(r);
+    cudaStreamSynchronize(r->stream);
+    cudaEventDestroy(r->staged);
+    cudaFreeHost(r->pinned);
+    delete r;
+}
+
+// ---------------------------------------------------------------------------
+// runs: seeding and reference
+
+static void pack_keys(const fq_key* keys, size_t n, size_t kb, std::vector<unsigned char>& out) {
+    out.resize(kb * n);
+    for (size_t i = 0; i < n; ++i) memcpy(out.data() + i * kb, &keys[i], kb);
+}
+
+extern "C" int fq_run_seed(fq_run* r, const fq_key* keys, const double* amps, size_t n,
+                           double shift, int64_t step) {
+    if (!r || (n && (!keys || !amps)) || !std::isfinite(shift)) return FQ_ERR_INVALID;
+    std::vector<size_t> idx;
+    idx.reserve(n);
+    for (size_t i = 0; i < n; ++i) {
+        if (!key_valid(&r->ham, keys[i]) || !std::isfinite(amps[i])) return FQ_ERR_INVALID;
+        if (r->amp == FQ_AMP_INT && (amps[i] != std::floor(amps[i]) || std::fabs(amps[i]) > 9.0e15))
+            return FQ_ERR_INVALID;
+        if (amps[i] != 0.0) idx.push_back(i);
+    }
+    std::sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return key_less(keys[a], keys[b]); });
+    for (size_t i = 1; i < idx.size(); ++i)
+        if (key_same(keys[idx[i - 1]], keys[idx[i]])) return FQ_ERR_INVALID;
+    const size_t m = idx.size();
+    std::vector<fq_key> sk(m);
+    std::vector<double> sa(m);
+    double norm = 0.0;
+    for (size_t i = 0; i < m; ++i) {
+        sk[i] = keys[idx[i]];
+        double a = amps[idx[i]];
+        if (r->amp == FQ_AMP_F32) a = (double)(float)a;
+        sa[i] = a;
+        norm += std::fabs(a);
+    }
+    if (m > (size_t)r->B * r->Cv) return FQ_ERR_CAPACITY;
+    CK(cudaStreamSynchronize(r->stream));
+    const size_t kb = r->ks->key_bytes;
+    std::vector<unsigned char> kbuf;
+    pack_keys(sk.data(), m, kb, kbuf);
+    void* d_k = nullptr;
+    double* d_a = nullptr;
+    CK(cudaMalloc(&d_k, kb * (m ? m : 1)));
+    CK(cudaMalloc((void**)&d_a, sizeof(double) * (m ? m : 1)));
+    RunState s0;
+    memset(&s0, 0, sizeof s0);
+    CK(cudaMemcpy(&s0, r->st, sizeof s0, cudaMemcpyDeviceToHost));
+    s0.shift = shift;
+    s0.norm = norm;
+    s0.step = step;
+    s0.len = (long long)m;
+    s0.cur = 0;
+    s0.err = 0;
+    s0.n_exact = s0.n_inexact = s0.n_spawns = 0;
+    s0.hist_head = 0;
+    s0.last_hproj = s0.last_vproj = 0.0;
+    s0.last_exact = s0.last_inexact = s0.last_spawns = 0;
+    cudaError_t e = cudaMemcpyAsync(r->st, &s0, sizeof s0, cudaMemcpyHostToDevice, r->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->vcount[0], 0, sizeof(unsigned) * r->B, r->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->vcount[1], 0, sizeof(unsigned) * r->B, r->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->sfill, 0, sizeof(unsigned) * r->B, r->stream);
+    if (e == cudaSuccess && m) e = cudaMemcpyAsync(d_k, kbuf.data(), kb * m, cudaMemcpyHostToDevice, r->stream);
+    if (e == cudaSuccess && m) e = cudaMemcpyAsync(d_a, sa.data(), sizeof(double) * m, cudaMemcpyHostToDevice, r->stream);
+    RunDesc hd;
+    fill_desc(r, hd, 0);
+    RunDesc* d_desc = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_desc, sizeof(RunDesc));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_desc, &hd, sizeof hd, cudaMemcpyHostToDevice, r->stream);
+    if (e == cudaSuccess) {
+        r->ks->seed(d_desc, d_k, d_a, m, r->stream);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+    unsigned err = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&err, &r->st->err, sizeof err, cudaMemcpyDeviceToHost);
+    cudaFree(d_k);
+    cudaFree(d_a);
+    cudaFree(d_desc);
+    if (e != cudaSuccess) return cuda_err(e);
+    if (err) {
+        unsigned z = 0;
+        cudaMemset(r->vcount[0], 0, sizeof(unsigned) * r->B);
+        cudaMemcpy(&r->st->err, &z, sizeof z, cudaMemcpyHostToDevice);
+        r->seeded = false;
+        return FQ_ERR_CAPACITY;
+    }
+    r->seeded = true;
+    r->hist_read = 0;
+    return FQ_OK;
+}
+
+extern "C" int fq_run_set_reference(fq_run* r, const fq_key* keys, const double* y, size_t n) {
+    if (!r || n > 64 || (n && (!keys || !y))) return FQ_ERR_INVALID;
+    for (size_t i = 0; i < n; ++i) {
+        if (!key_valid(&r->ham, keys[i]) || !std::isfinite(y[i])) return FQ_ERR_INVALID;
+        for (size_t j = 0; j < i; ++j)
+            if (key_same(keys[i], keys[j])) return FQ_ERR_INVALID;
+    }
+    CK(cudaStreamSynchronize(r->stream));
+    const size_t kb = r->ks->key_bytes;
+    const unsigned B = r->B;
+    if (n == 0) {
+        CK(cudaMemset(r->ref_off, 0, sizeof(unsigned) * (B + 1)));
+        return FQ_OK;
+    }
+    std::vector<unsigned char> kbuf;
+    pack_keys(keys, n, kb, kbuf);
+    void *d_refs = nullptr, *d_tk = nullptr;
+    double *d_y = nullptr, *d_th = nullptr, *d_tv = nullptr;
+    unsigned *d_cnt = nullptr, *d_off = nullptr, *d_tseg = nullptr;
+    CK(cudaMalloc(&d_refs, kb * n));
+    CK(cudaMalloc((void**)&d_y, sizeof(double) * n));
+    CK(cudaMalloc((void**)&d_cnt, sizeof(unsigned) * n));
+    CK(cudaMemcpy(d_refs, kbuf.data(), kb * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_y, y, sizeof(double) * n, cudaMemcpyHostToDevice));
+    r->ks->ref_count(r->ham.mp, d_refs, (int)n, d_cnt, 0);
+    std::vector<unsigned> cnt(n), off(n + 1, 0);
+    CK(cudaMemcpy(cnt.data(), d_cnt, sizeof(unsigned) * n, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i) off[i + 1] = off[i] + cnt[i];
+    const size_t T = off[n];
+    CK(cudaMalloc((void**)&d_off, sizeof(unsigned) * (n + 1)));
+    CK(cudaMalloc(&d_tk, kb * T));
+    CK(cudaMalloc((void**)&d_th, sizeof(double) * T));
+    CK(cudaMalloc((void**)&d_tv, sizeof(double) * T));
+    CK(cudaMalloc((void**)&d_tseg, sizeof(unsigned) * T));
+    CK(cudaMemcpy(d_off, off.data(), sizeof(unsigned) * (n + 1), cudaMemcpyHostToDevice));
+    r->ks->ref_terms(r->ham.mp, d_refs, d_y, (int)n, d_off, d_tk, d_th, d_tv, d_tseg, r->log2B, 0);
+    CK(cudaDeviceSynchronize());
+    std::vector<unsigned char> tk(kb * T);
+    std::vector<double> th(T), tv(T);
+    std::vector<unsigned> tseg(T);
+    CK(cudaMemcpy(tk.data(), d_tk, kb * T, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(th.data(), d_th, sizeof(double) * T, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(tv.data(), d_tv, sizeof(double) * T, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(tseg.data(), d_tseg, sizeof(unsigned) * T, cudaMemcpyDeviceToHost));
+    cudaFree(d_refs); cudaFree(d_y); cudaFree(d_cnt); cudaFree(d_off);
+    cudaFree(d_tk); cudaFree(d_th); cudaFree(d_tv); cudaFree(d_tseg);
+    // group the terms by segment (stable), so each merge block finds its own
+    std::vector<size_t> order(T);
+    for (size_t i = 0; i < T; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return tseg[a] < tseg[b]; });
+    std::vector<unsigned char> sk(kb * T);
+    std::vector<double> sh(T), sv(T);
+    std::vector<unsigned> soff(B + 1, 0);
+    for (size_t i = 0; i < T; ++i) {
+        memcpy(sk.data() + i * kb, tk.data() + order[i] * kb, kb);
+        sh[i] = th[order[i]];
+        sv[i] = tv[order[i]];
+        soff[tseg[order[i]] + 1]++;
+    }
+    for (unsigned b = 0; b < B; ++b) soff[b + 1] += soff[b];
+    if (T > r->ref_cap) {
+        // the reference arrays are rarely resized; they live as long as the run
+        r->ref_keys = dev_alloc(r, kb * T);
+        r->ref_h = (double*)dev_alloc(r, sizeof(double) * T);
+        r->ref_v = (double*)dev_alloc(r, sizeof(double) * T);
+        if (!r->ref_keys || !r->ref_h || !r->ref_v) return FQ_ERR_NOMEM;
+        r->ref_cap = T;
+        r->gen++;
+    }
+    CK(cudaMemcpy(r->ref_keys, sk.data(), kb * T, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(r->ref_h, sh.data(), sizeof(double) * T, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(r->ref_v, sv.data(), sizeof(double) * T, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(r->ref_off, soff.data(), sizeof(unsigned) * (B + 1), cudaMemcpyHostToDevice));
+    return FQ_OK;
+}
+
+extern "C" int fq_run_seed_default(fq_run* r, double weight) {
+    if (!r || !(weight != 0.0) || !std::isfinite(weight)) return FQ_ERR_INVALID;
+    fq_key s;
+    int rc = fq_ham_starting_address(&r->ham, &s);
+    if (rc) return rc;
+    double diag = 0;
+    size_t m = 0;
+    rc = ham_column_dev(&r->ham, r->amp, s, &diag, nullptr, nullptr, 0, &m, r->stream);
+    if (rc) return rc;
+    rc = fq_run_seed(r, &s, &weight, 1, diag, 0);
+    if (rc) return rc;
+    return fq_run_set_reference(r, &s, &weight, 1);
+}
+
+static int set_state_field(fq_run* r, size_t offset, double v) {
+    if (!r || !std::isfinite(v)) return FQ_ERR_INVALID;
+    // ordered with queued steps: the value is staged in the run's pinned slot,
+    // which is reused only after the copy has completed
+    CK(cudaEventSynchronize(r->staged));
+    *r->pinned = v;
+    CK(cudaMemcpyAsync((char*)r->st + offset, r->pinned, sizeof(double), cudaMemcpyHostToDevice,
+                       r->stream));
+    CK(cudaEventRecord(r->staged, r->stream));
+    return FQ_OK;
+}
+
+extern "C" int fq_run_set_dt(fq_run* r, double dt) {
+    if (!(dt > 0)) return FQ_ERR_INVALID;
+    return set_state_field(r, offsetof(RunState, dt), dt);
+}
+extern "C" int fq_run_set_shift(fq_run* r, double s) { return set_state_field(r, offsetof(RunState, shift), s); }
+extern "C" int fq_run_set_target(fq_run* r, double t) {
+    if (!(t > 0)) return FQ_ERR_INVALID;
+    return set_state_field(r, offsetof(RunState, target), t);
+}
+
+// ---------------------------------------------------------------------------
+// batches: descriptor table, graphs, stepping
+
+static void enqueue_steps(fq_batch* b, int n, cudaStream_t s) {
+    const int nr = (int)b->runs.size();
+    for (int i = 0; i < n; ++i) {
+        b->ks->spawn(b->cfg, b->d_desc, b->d_seg_run, b->G, s);
+        b->ks->merge(b->cfg, b->d_desc, b->d_seg_run, b->G, s);
+        launch_shift(b->d_desc, nr, s);
+    }
+}
+
+static void batch_free(fq_batch* b) {
+    if (!b) return;
+    if (b->g1) cudaGraphExecDestroy(b->g1);
+    if (b->g16) cudaGraphExecDestroy(b->g16);
+    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->d_seg_run) cudaFree(b->d_seg_run);
+    delete b;
+}
+
+static int capture(fq_batch* b, int n, cudaGraphExec_t* out) {
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        enqueue_steps(b, n, cs);
+        e = cudaStreamEndCapture(cs, &g);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    return cuda_err(e);
+}
+
+static int batch_build(fq_batch* b) {
+    const size_t nr = b->runs.size();
+    b->gens.resize(nr);
+    for (size_t i = 0; i < nr; ++i) b->gens[i] = b->runs[i]->gen;
+    std::vector<RunDesc> desc(nr);
+    std::vector<unsigned> seg_run;
+    unsigned base = 0, slots = 512;
+    for (size_t i = 0; i < nr; ++i) {
+        fq_run* r = b->runs[i];
+        fill_desc(r, desc[i], base);
+        for (unsigned s = 0; s < r->B; ++s) seg_run.push_back((unsigned)i);
+        base += r->B;
+        slots = std::max(slots, r->slots);
+    }
+    b->G = base;
+    CK(cudaMalloc((void**)&b->d_desc, sizeof(RunDesc) * nr));
+    CK(cudaMalloc((void**)&b->d_seg_run, sizeof(unsigned) * base));
+    CK(cudaMemcpy(b->d_desc, desc.data(), sizeof(RunDesc) * nr, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b->d_seg_run, seg_run.data(), sizeof(unsigned) * base, cudaMemcpyHostToDevice));
+    const size_t smem = (size_t)slots * (b->ks->key_bytes + b->ks->acc_bytes);
+    CK(b->ks->prepare(smem));
+    if (nr == 1 && b->runs[0]->has_tuned && b->runs[0]->tuned.slots == slots) b->cfg = b->runs[0]->tuned;
+    else b->cfg = default_cfg(b->ks, slots, b->G);
+    int rc = capture(b, 1, &b->g1);
+    if (!rc) rc = capture(b, 16, &b->g16);
+    return rc;
+}
+
+static int batch_new(fq_run* const* runs, int n, bool owned, fq_batch** out) {
+    fq_batch* b = new (std::nothrow) fq_batch();
+    if (!b) return FQ_ERR_NOMEM;
+    b->runs.assign(runs, runs + n);
+    b->ks = runs[0]->ks;
+    b->stream = runs[0]->stream;
+    b->owned_by_run = owned;
+    b->d_desc = nullptr;
+    b->d_seg_run = nullptr;
+    b->g1 = b->g16 = nullptr;
+    int rc = batch_build(b);
+    if (rc) {
+        batch_free(b);
+        return rc;
+    }
+    *out = b;
+    return FQ_OK;
+}
+
+static int batch_refresh(fq_batch* b) {
+    bool stale = false;
+    for (size_t i = 0; i < b->runs.size(); ++i) stale |= b->gens[i] != b->runs[i]->gen;
+    if (!stale) return FQ_OK;
+    CK(cudaStreamSynchronize(b->stream));
+    if (b->g1) cudaGraphExecDestroy(b->g1);
+    if (b->g16) cudaGraphExecDestroy(b->g16);
+    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->d_seg_run) cudaFree(b->d_seg_run);
+    b->g1 = b->g16 = nullptr;
+    b->d_desc = nullptr;
+    b->d_seg_run = nullptr;
+    return batch_build(b);
+}
+
+static int batch_launch(fq_batch* b, int64_t n) {
+    if (n < 0) return FQ_ERR_INVALID;
+    int rc = batch_refresh(b);
+    if (rc) return rc;
+    while (n >= 16) {
+        CK(cudaGraphLaunch(b->g16, b->stream));
+        n -= 16;
+    }
+    while (n-- > 0) CK(cudaGraphLaunch(b->g1, b->stream));
+    return FQ_OK;
+}
+
+static int single_batch(fq_run* r) {
+    if (r->single) return FQ_OK;
+    fq_run* one[1] = {r};
+    return batch_new(one, 1, true, &r->single);
+}
+
+extern "C" int fq_run_step(fq_run* r, int64_t n) {
+    if (!r || n < 0) return FQ_ERR_INVALID;
+    if (!r->seeded) return FQ_ERR_INVALID;
+    int rc = single_batch(r);
+    if (rc) return rc;
+    return batch_launch(r->single, n);
+}
+
+// read the device error; on error roll the run back to its last completed
+// step (the current buffer and state are untouched by a failed step)
+static int run_check(fq_run* r) {
+    CK(cudaStreamSynchronize(r->stream));
+    unsigned err = 0;
+    CK(cudaMemcpy(&err, &r->st->err, sizeof err, cudaMemcpyDeviceToHost));
+    if (!err) return FQ_OK;
+    RunState s;
+    CK(cudaMemcpy(&s, r->st, sizeof s, cudaMemcpyDeviceToHost));
+    s.err = 0;
+    s.n_exact = s.n_inexact = s.n_spawns = 0;
+    CK(cudaMemcpy(r->st, &s, sizeof s, cudaMemcpyHostToDevice));
+    CK(cudaMemset(r->sfill, 0, sizeof(unsigned) * r->B));
+    if (err & FQ_DERR_EMPTY) return FQ_ERR_EMPTY;
+    if (err & FQ_DERR_TIMEOUT) return FQ_ERR_TIMEOUT;
+    return FQ_ERR_CAPACITY;
+}
+
+extern "C" int fq_run_sync(fq_run* r) {
+    if (!r) return FQ_ERR_INVALID;
+    return run_check(r);
+}
+
+extern "C" int fq_run_stats(fq_run* r, fq_stats* out) {
+    if (!r || !out) return FQ_ERR_INVALID;
+    const int rc = run_check(r);
+    RunState s;
+    CK(cudaMemcpy(&s, r->st, sizeof s, cudaMemcpyDeviceToHost));
+    out->step = s.step;
+    out->len = s.len;
+    out->exact_steps = s.last_exact;
+    out->inexact_steps = s.last_inexact;
+    out->n_spawns = s.last_spawns;
+    out->shift = s.shift;
+    out->norm = s.norm;
+    out->hproj = s.last_hproj;
+    out->vproj = s.last_vproj;
+    return rc;
+}
+
+extern "C" int fq_run_history(fq_run* r, fq_stats* out, size_t cap, size_t* n) {
+    if (!r || !n || (cap && !out)) return FQ_ERR_INVALID;
+    *n = 0;
+    const int rc = run_check(r);
+    unsigned long long head = 0;
+    CK(cudaMemcpy(&head, &r->st->hist_head, sizeof head, cudaMemcpyDeviceToHost));
+    unsigned long long first = r->hist_read;
+    if (head > FQ_HIST_CAP && first < head - FQ_HIST_CAP) first = head - FQ_HIST_CAP;
+    size_t cnt = (size_t)std::min<unsigned long long>(head - first, cap);
+    static_assert(sizeof(StatsRow) == sizeof(fq_stats), "row layout");
+    for (size_t i = 0; i < cnt;) {
+        const unsigned pos = (unsigned)((first + i) % FQ_HIST_CAP);
+        const size_t chunk = std::min<size_t>(cnt - i, FQ_HIST_CAP - pos);
+        CK(cudaMemcpy(out + i, r->hist + pos, sizeof(StatsRow) * chunk, cudaMemcpyDeviceToHost));
+        i += chunk;
+    }
+    r->hist_read = first + cnt;
+    *n = cnt;
+    return rc;
+}
+
+// gather the segmented arrays (counts `cnt_dev`, capacity `cap`) to the host
+static int gather(fq_run* r, const void* keys, const void* vals, unsigned cap, const unsigned* cnt_dev,
+                  bool spawns, std::vector<fq_key>& ok, std::vector<double>& ov) {
+    const unsigned B = r->B;
+    std::vector<unsigned> cnt(B), off(B + 1, 0);
+    CK(cudaMemcpy(cnt.data(), cnt_dev, sizeof(unsigned) * B, cudaMemcpyDeviceToHost));
+    for (unsigned b = 0; b < B; ++b) off[b + 1] = off[b] + std::min(cnt[b], cap);
+    const size_t T = off[B];
+    const size_t kb = r->ks->key_bytes;
+    ok.assign(T, fq_key{0, 0});
+    ov.assign(T, 0.0);
+    if (!T) return FQ_OK;
+    unsigned* d_off = nullptr;
+    void* d_k = nullptr;
+    double* d_v = nullptr;
+    CK(cudaMalloc((void**)&d_off, sizeof(unsigned) * (B + 1)));
+    CK(cudaMalloc(&d_k, kb * T));
+    CK(cudaMalloc((void**)&d_v, sizeof(double) * T));
+    CK(cudaMemcpy(d_off, off.data(), sizeof(unsigned) * (B + 1), cudaMemcpyHostToDevice));
+    if (spawns) r->ks->gather_spawns(keys, vals, cap, cnt_dev, d_off, B, d_k, d_v, 0);
+    else r->ks->gather_vec(keys, vals, cap, cnt_dev, d_off, B, d_k, d_v, 0);
+    CK(cudaDeviceSynchronize());
+    std::vector<unsigned char> kbuf(kb * T);
+    CK(cudaMemcpy(kbuf.data(), d_k, kb * T, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(ov.data(), d_v, sizeof(double) * T, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < T; ++i) memcpy(&ok[i], kbuf.data() + i * kb, kb);
+    cudaFree(d_off); cudaFree(d_k); cudaFree(d_v);
+    return FQ_OK;
+}
+
+extern "C" int fq_run_export(fq_run* r, fq_key* keys, double* amps, size_t cap, size_t* n) {
+    if (!r || !n || (cap && (!keys || !amps))) return FQ_ERR_INVALID;
+    *n = 0;
+    const int rc = run_check(r);
+    int cur = 0;
+    CK(cudaMemcpy(&cur, &r->st->cur, sizeof cur, cudaMemcpyDeviceToHost));
+    std::vector<fq_key> k;
+    std::vector<double> v;
+    int g = gather(r, r->vkeys[cur], r->vamps[cur], r->Cv, r->vcount[cur], false, k, v);
+    if (g) return g;
+    std::vector<size_t> order(k.size());
+    for (size_t i = 0; i < k.size(); ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](size_t a, size_t b) { return key_less(k[a], k[b]); });
+    const size_t w = std::min(cap, k.size());
+    for (size_t i = 0; i < w; ++i) {
+        keys[i] = k[order[i]];
+        amps[i] = v[order[i]];
+    }
+    *n = k.size();
+    return rc;
+}
+
+extern "C" int fq_run_spawns(fq_run* r, fq_key* dest, double* val, size_t cap, size_t* n) {
+    if (!r || !n || (cap && (!dest || !val))) return FQ_ERR_INVALID;
+    *n = 0;
+    int rc = run_check(r);
+    if (rc) return rc;
+    if (!r->seeded) return FQ_ERR_INVALID;
+    rc = single_batch(r);
+    if (!rc) rc = batch_refresh(r->single);
+    if (rc) return rc;
+    fq_batch* b = r->single;
+    b->ks->spawn(b->cfg, b->d_desc, b->d_seg_run, b->G, r->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(r->stream));
+    unsigned err = 0;
+    CK(cudaMemcpy(&err, &r->st->err, sizeof err, cudaMemcpyDeviceToHost));
+    std::vector<fq_key> k;
+    std::vector<double> v;
+    if (!err) {
+        int g = gather(r, r->skeys, r->samps, r->Cs, r->sfill, true, k, v);
+        if (g) return g;
+    }
+    rc = run_check(r);  // clears the error flag if one was set
+    CK(cudaMemset(r->sfill, 0, sizeof(unsigned) * r->B));
+    RunState s;
+    CK(cudaMemcpy(&s, r->st, sizeof s, cudaMemcpyDeviceToHost));
+    s.n_exact = s.n_inexact = s.n_spawns = 0;
+    CK(cudaMemcpy(r->st, &s, sizeof s, cudaMemcpyHostToDevice));
+    if (err) return FQ_ERR_CAPACITY;
+    const size_t w = std::min(cap, k.size());
+    for (size_t i = 0; i < w; ++i) {
+        dest[i] = k[i];
+        val[i] = v[i];
+    }
+    *n = k.size();
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// autotuning: time each launch shape over real steps, keep the fastest
+
+static int autotune(fq_batch* b, int steps) {
+    if (steps < 1) return FQ_ERR_INVALID;
+    const int sms = num_sms();
+    const size_t smem = (size_t)b->cfg.slots * (b->ks->key_bytes + b->ks->acc_bytes);
+    std::vector<LaunchCfg> cands;
+    for (int sb : {256, 512})
+        for (int sw : {1, 2})
+            for (int mb : {256, 512}) {
+                const int os = b->ks->spawn_occupancy(sb);
+                const int om = b->ks->merge_occupancy(mb, smem);
+                if (os < 1 || om < 1) continue;
+                LaunchCfg c = b->cfg;
+                c.spawn_block = sb;
+                c.spawn_grid = (int)std::max<long long>(
+                    1, std::min<long long>((long long)sms * os * sw / 2, b->G));
+                c.merge_block = mb;
+                c.merge_grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * om, b->G));
+                cands.push_back(c);
+            }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    LaunchCfg bestc = b->cfg;
+    for (const LaunchCfg& c : cands) {
+        b->cfg = c;
+        enqueue_steps(b, 1, b->stream);  // warm
+        cudaEventRecord(e0, b->stream);
+        enqueue_steps(b, steps, b->stream);
+        cudaEventRecord(e1, b->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            bestc = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->cfg = bestc;
+    if (b->g1) cudaGraphExecDestroy(b->g1);
+    if (b->g16) cudaGraphExecDestroy(b->g16);
+    b->g1 = b->g16 = nullptr;
+    int rc = capture(b, 1, &b->g1);
+    if (!rc) rc = capture(b, 16, &b->g16);
+    return rc;
+}
+
+extern "C" int fq_run_autotune(fq_run* r, int steps) {
+    if (!r || !r->seeded) return FQ_ERR_INVALID;
+    int rc = single_batch(r);
+    if (!rc) rc = batch_refresh(r->single);
+    if (rc) return rc;
+    rc = autotune(r->single, steps);
+    if (rc) return rc;
+    r->tuned = r->single->cfg;
+    r->has_tuned = true;
+    return run_check(r);
+}
+
+extern "C" int fq_run_profile(fq_run* r, int n, float* ms) {
+    if (!r || !ms || n < 1 || n > 4096 || !r->seeded) return FQ_ERR_INVALID;
+    int rc = single_batch(r);
+    if (!rc) rc = batch_refresh(r->single);
+    if (rc) return rc;
+    fq_batch* b = r->single;
+    std::vector<cudaEvent_t> ev((size_t)4 * n, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < ev.size() && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        cudaEventRecord(ev[4 * i], r->stream);
+        b->ks->spawn(b->cfg, b->d_desc, b->d_seg_run, b->G, r->stream);
+        cudaEventRecord(ev[4 * i + 1], r->stream);
+        b->ks->merge(b->cfg, b->d_desc, b->d_seg_run, b->G, r->stream);
+        cudaEventRecord(ev[4 * i + 2], r->stream);
+        launch_shift(b->d_desc, 1, r->stream);
+        e = cudaEventRecord(ev[4 * i + 3], r->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+    double acc[3] = {0, 0, 0};
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+        for (int k = 0; k < 3; ++k) {
+            float t = 0;
+            e = cudaEventElapsedTime(&t, ev[4 * i + k], ev[4 * i + k + 1]);
+            acc[k] += t;
+        }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    if (e != cudaSuccess) return cuda_err(e);
+    for (int k = 0; k < 3; ++k) ms[k] = (float)(acc[k] / n);
+    return run_check(r);
+}
+
+// ---------------------------------------------------------------------------
+// C ABI: batches
+
+extern "C" int fq_batch_create(fq_batch** out, fq_run* const* runs, int B) {
+    if (!out || !runs || B < 1) return FQ_ERR_INVALID;
+    *out = nullptr;
+    for (int i = 0; i < B; ++i) {
+        if (!runs[i] || !runs[i]->seeded) return FQ_ERR_INVALID;
+        if (runs[i]->ks != runs[0]->ks || runs[i]->stream != runs[0]->stream) return FQ_ERR_INVALID;
+        for (int j = 0; j < i; ++j)
+            if (runs[j] == runs[i]) return FQ_ERR_INVALID;
+    }
+    return batch_new(runs, B, false, out);
+}
+
+extern "C" void fq_batch_destroy(fq_batch* b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    batch_free(b);
+}
+
+extern "C" int fq_batch_step(fq_batch* b, int64_t n) {
+    if (!b) return FQ_ERR_INVALID;
+    return batch_launch(b, n);
+}
+
+extern "C" int fq_batch_sync(fq_batch* b) {
+    if (!b) return FQ_ERR_INVALID;
+    int rc = FQ_OK;
+    for (fq_run* r : b->runs) {
+        int e = run_check(r);
+        if (e && !rc) rc = e;
+    }
+    return rc;
+}
+
+extern "C" int fq_batch_autotune(fq_batch* b, int steps) {
+    if (!b) return FQ_ERR_INVALID;
+    int rc = autotune(b, steps);
+    if (rc) return rc;
+    return fq_batch_sync(b);
+}

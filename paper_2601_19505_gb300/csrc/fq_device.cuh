@@ -1,0 +1,339 @@
+// fq_device.cuh -- device-side building blocks of the FCIQMC step:
+// Fock-address bit operations, the Bose-Hubbard Hamiltonians evaluated
+// column by column, Philox4x32-10 draws keyed by content, and hashing.
+//
+// Addresses (Sec. 6.1 of the Rimu.jl paper): a bit string of N + M - 1 bits,
+// n_m ones for mode m, one zero between consecutive modes, mode 0 at the
+// least significant bit.  Keys are uint64_t when N + M - 1 <= 64, else
+// unsigned __int128.  Every bit that is not part of the address is 0, so
+// the M - 1 separators are the M - 1 lowest zero bits of the key.
+//
+// Everything here is compiled without FMA contraction (--fmad=false) so that
+// each floating-point expression rounds exactly as written.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fq_shared.h"
+
+namespace fq {
+
+typedef unsigned __int128 u128;
+
+// ---------------------------------------------------------------------------
+// bit helpers
+
+__device__ __forceinline__ int nth_set64(uint64_t x, int j) {
+    // position of the j-th (0-based) set bit of x; requires j < popc(x)
+    int pos = 0, c;
+    c = __popc((unsigned)x);
+    if (j >= c) { j -= c; x >>= 32; pos += 32; }
+    c = __popc((unsigned)(x & 0xFFFFu));
+    if (j >= c) { j -= c; x >>= 16; pos += 16; }
+    c = __popc((unsigned)(x & 0xFFu));
+    if (j >= c) { j -= c; x >>= 8; pos += 8; }
+    c = __popc((unsigned)(x & 0xFu));
+    if (j >= c) { j -= c; x >>= 4; pos += 4; }
+    c = __popc((unsigned)(x & 0x3u));
+    if (j >= c) { j -= c; x >>= 2; pos += 2; }
+    c = (int)(x & 1u);
+    if (j >= c) pos += 1;
+    return pos;
+}
+
+template <class K> struct KeyOps;
+
+template <> struct KeyOps<uint64_t> {
+    static constexpr int W = 64;
+    __device__ __forceinline__ static uint64_t empty() { return ~0ull; }
+    __device__ __forceinline__ static int popc(uint64_t k) { return __popcll(k); }
+    __device__ __forceinline__ static int nth(uint64_t k, int j) { return nth_set64(k, j); }
+    __device__ __forceinline__ static uint64_t shr(uint64_t x, int s) { return s >= 64 ? 0ull : x >> s; }
+    __device__ __forceinline__ static uint64_t shl(uint64_t x, int s) { return s >= 64 ? 0ull : x << s; }
+    __device__ __forceinline__ static uint64_t low(int p) { return p >= 64 ? ~0ull : ((1ull << p) - 1ull); }
+    __device__ __forceinline__ static int ctz(uint64_t x) { return x ? __ffsll((long long)x) - 1 : 64; }
+    __device__ __forceinline__ static uint64_t bit(int p) { return 1ull << p; }
+    __device__ __forceinline__ static uint64_t rng_h(uint64_t k) { return k; }
+};
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+    // splitmix64 (Steele, Lea, Flood 2014)
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+template <> struct KeyOps<u128> {
+    static constexpr int W = 128;
+    __device__ __forceinline__ static u128 empty() { return ~(u128)0; }
+    __device__ __forceinline__ static int popc(u128 k) {
+        return __popcll((uint64_t)k) + __popcll((uint64_t)(k >> 64));
+    }
+    __device__ __forceinline__ static int nth(u128 k, int j) {
+        uint64_t lo = (uint64_t)k;
+        int c = __popcll(lo);
+        return j < c ? nth_set64(lo, j) : 64 + nth_set64((uint64_t)(k >> 64), j - c);
+    }
+    __device__ __forceinline__ static u128 shr(u128 x, int s) { return s >= 128 ? (u128)0 : x >> s; }
+    __device__ __forceinline__ static u128 shl(u128 x, int s) { return s >= 128 ? (u128)0 : x << s; }
+    __device__ __forceinline__ static u128 low(int p) { return p >= 128 ? ~(u128)0 : (((u128)1 << p) - 1); }
+    __device__ __forceinline__ static int ctz(u128 x) {
+        uint64_t lo = (uint64_t)x, hi = (uint64_t)(x >> 64);
+        if (lo) return __ffsll((long long)lo) - 1;
+        if (hi) return 64 + __ffsll((long long)hi) - 1;
+        return 128;
+    }
+    __device__ __forceinline__ static u128 bit(int p) { return (u128)1 << p; }
+    __device__ __forceinline__ static uint64_t rng_h(u128 k) {
+        return (uint64_t)k ^ splitmix64((uint64_t)(k >> 64));
+    }
+};
+
+// start bit of mode s (0-based): one past the s-th separator
+template <class K> __device__ __forceinline__ int mode_start(K k, int s) {
+    return s == 0 ? 0 : KeyOps<K>::nth(~k, s - 1) + 1;
+}
+// length of the run of ones starting at bit p
+template <class K> __device__ __forceinline__ int run_from(K k, int p) {
+    return KeyOps<K>::ctz(~KeyOps<K>::shr(k, p));
+}
+template <class K> __device__ __forceinline__ int mode_occ(K k, int s) {
+    return run_from(k, mode_start(k, s));
+}
+// remove the bit at p, shifting the higher bits down
+template <class K> __device__ __forceinline__ K del_bit(K x, int p) {
+    typedef KeyOps<K> O;
+    return (x & O::low(p)) | O::shl(O::shr(x, p + 1), p);
+}
+// insert a one at p, shifting bits >= p up
+template <class K> __device__ __forceinline__ K ins_one(K x, int p) {
+    typedef KeyOps<K> O;
+    return (x & O::low(p)) | O::bit(p) | O::shl(O::shr(x, p), p + 1);
+}
+template <class K> __device__ __forceinline__ K remove_boson(K k, int s) {
+    return del_bit(k, mode_start(k, s));
+}
+template <class K> __device__ __forceinline__ K add_boson(K k, int s) {
+    return ins_one(k, mode_start(k, s));
+}
+// bits that start a run of ones: one per occupied mode
+template <class K> __device__ __forceinline__ K run_starts(K k) { return k & ~(k << 1); }
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and the draw layout:
+//   key     = (seed_lo32, seed_hi32 ^ run_id * 0x9E3779B9)
+//   counter = (step, stream, h_lo32, h_hi32), h = KeyOps<K>::rng_h(address)
+//   stream  = attempt index for picks, 0xFFFFFFFF for vector compression,
+//             0xFFFFFFFE for integer diagonal rounding
+
+__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+        const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 draw(uint2 key, unsigned step, unsigned stream, uint64_t h) {
+    return philox10(make_uint4(step, stream, (unsigned)h, (unsigned)(h >> 32)), key);
+}
+// uniform in [0, 1) with 53 random bits, exact in FP64
+__device__ __forceinline__ double uniform53(uint4 w) {
+    return ((double)(w.x >> 5) * 67108864.0 + (double)(w.y >> 6)) * (1.0 / 9007199254740992.0);
+}
+// index in [0, m)
+__device__ __forceinline__ unsigned pick(uint4 w, unsigned m) {
+    return (unsigned)(((unsigned long long)w.z * (unsigned long long)m) >> 32);
+}
+
+// murmur3 64-bit finaliser (Appleby): segment = top bits, table slot = low bits
+__device__ __forceinline__ uint64_t fmix64(uint64_t h) {
+    h ^= h >> 33;
+    h *= 0xFF51AFD7ED558CCDull;
+    h ^= h >> 33;
+    h *= 0xC4CEB9FE1A85EC53ull;
+    h ^= h >> 33;
+    return h;
+}
+__device__ __forceinline__ unsigned segment_of(uint64_t mixed, int log2B) {
+    return log2B ? (unsigned)(mixed >> (64 - log2B)) : 0u;
+}
+
+// ---------------------------------------------------------------------------
+// Hamiltonians
+
+template <int KIND> struct Model;
+
+// Real space (Eq. bose-hubbard-hamiltonian): H_ii = (u/2) sum n(n-1); each
+// (direction, occupied site) pair hops one boson to a neighbour with value
+// -t sqrt(n_s (n_s' + 1)).  Entry k: direction k / n_occ, occupied site
+// k mod n_occ (ascending); directions (+1, -1) in 1D, (+x, -x, +y, -y) in 2D.
+template <int KIND> struct RealModel {
+    static constexpr int Z = KIND == FQ_KIND_REAL_1D ? 2 : 4;
+
+    __device__ __forceinline__ static int neighbour(const ModelParams& p, int s, int d) {
+        if (KIND == FQ_KIND_REAL_1D) return d == 0 ? (s + 1 == p.M ? 0 : s + 1) : (s == 0 ? p.M - 1 : s - 1);
+        int x = s % p.Lx, y = s / p.Lx;
+        if (d == 0) x = x + 1 == p.Lx ? 0 : x + 1;
+        else if (d == 1) x = x == 0 ? p.Lx - 1 : x - 1;
+        else if (d == 2) y = y + 1 == p.Ly ? 0 : y + 1;
+        else y = y == 0 ? p.Ly - 1 : y - 1;
+        return x + p.Lx * y;
+    }
+
+    struct Col {  // per-source data reused by every pick of a column
+        int n_occ;
+    };
+
+    template <class K> __device__ __forceinline__ static double diagonal(const ModelParams& p, K k) {
+        K st = run_starts(k);
+        long long s = 0;
+        while (st) {
+            int P = KeyOps<K>::ctz(st);
+            long long n = run_from(k, P);
+            s += n * (n - 1);
+            st &= st - 1;
+        }
+        return (p.u * 0.5) * (double)s;
+    }
+    template <class K> __device__ __forceinline__ static unsigned num_offdiag(const ModelParams&, K k, Col& c) {
+        c.n_occ = KeyOps<K>::popc(run_starts(k));
+        return (unsigned)(Z * c.n_occ);
+    }
+    // k-th off-diagonal entry of the column at `key`
+    template <class K>
+    __device__ __forceinline__ static K offdiag(const ModelParams& p, K key, const Col& c, unsigned kk,
+                                                double& val) {
+        const int d = (int)(kk / (unsigned)c.n_occ), r = (int)(kk % (unsigned)c.n_occ);
+        const int P = KeyOps<K>::nth(run_starts(key), r);
+        const int s = P - KeyOps<K>::popc(key & KeyOps<K>::low(P));
+        const int ns = run_from(key, P);
+        const int s2 = neighbour(p, s, d);
+        const int nt = mode_occ(key, s2);
+        val = -(p.t * sqrt((double)(ns * (nt + 1))));
+        return add_boson(del_bit(key, P), s2);
+    }
+};
+
+// Momentum space (Sec. 6.3): H = sum eps_k n_k + (u/2M) sum_{p,k,q}
+// a+_{p+q} a+_{k-q} a_k a_p.  Diagonal: sum eps n + (u/2M)(2N^2 - N - sum n^2).
+// Off-diagonal entries move an annihilated pair {p, q} to a created pair
+// {r, s}, r + s = p + q (mod M), {r,s} != {p,q}.  Enumeration order:
+// same-parity pairs (distinct even modes, distinct odd modes, double
+// occupancies) each with cE created pairs, then (even, odd) pairs with cO;
+// created pairs in ascending r with the identity skipped.  The pick is
+// unranked in O(1) from bit masks instead of walking the list.
+struct MomModel {
+    struct Col {
+        uint64_t occm, ge2;  // occupied modes, modes with n >= 2
+        int a, b, D;         // #occupied even modes, #odd modes, #double occupancies
+        unsigned ne, no;     // #same-parity pairs, #(even,odd) pairs
+        unsigned cE, cO;     // created pairs per annihilated pair of each class
+    };
+
+    template <class K> __device__ __forceinline__ static double diagonal(const ModelParams& p, K k) {
+        K st = run_starts(k);
+        double kin = 0.0;
+        long long sq = 0;
+        while (st) {
+            int P = KeyOps<K>::ctz(st);
+            int s = P - KeyOps<K>::popc(k & KeyOps<K>::low(P));
+            long long n = run_from(k, P);
+            kin += p.eps[s] * (double)n;
+            sq += n * n;
+            st &= st - 1;
+        }
+        long long N = p.N;
+        long long ic = 2 * N * N - N - sq;
+        return kin + p.g * (double)ic;
+    }
+
+    __device__ __forceinline__ static unsigned pairs_for(int M, int P) {
+        // unordered {r <= s} with r + s = P (mod M), P in [0, M)
+        return (unsigned)(P / 2 + 1 + (P + M) / 2 - P);
+    }
+
+    template <class K> __device__ __forceinline__ static unsigned num_offdiag(const ModelParams& p, K k, Col& c) {
+        K st = run_starts(k);
+        uint64_t occm = 0, ge2 = 0;
+        while (st) {
+            int P = KeyOps<K>::ctz(st);
+            int s = P - KeyOps<K>::popc(k & KeyOps<K>::low(P));
+            occm |= 1ull << s;
+            if (run_from(k, P) >= 2) ge2 |= 1ull << s;
+            st &= st - 1;
+        }
+        c.occm = occm; c.ge2 = ge2;
+        c.a = __popcll(occm & 0x5555555555555555ull);
+        c.b = __popcll(occm & 0xAAAAAAAAAAAAAAAAull);
+        c.D = __popcll(ge2);
+        c.ne = (unsigned)(c.a * (c.a - 1) / 2 + c.b * (c.b - 1) / 2 + c.D);
+        c.no = (unsigned)(c.a * c.b);
+        c.cE = pairs_for(p.M, 0) - 1;
+        c.cO = pairs_for(p.M, 1 % p.M) - 1;
+        return c.ne * c.cE + c.no * c.cO;
+    }
+
+    __device__ __forceinline__ static void tri_unrank(unsigned t, int n, int& i, int& j) {
+        // t-th pair (i < j) of n items in lexicographic order
+        i = 0;
+        while (t >= (unsigned)(n - 1 - i)) { t -= (unsigned)(n - 1 - i); ++i; }
+        j = i + 1 + (int)t;
+    }
+
+    template <class K>
+    __device__ __forceinline__ static K offdiag(const ModelParams& pm, K key, const Col& c, unsigned kk,
+                                                double& val) {
+        const int M = pm.M;
+        const uint64_t E = c.occm & 0x5555555555555555ull, O = c.occm & 0xAAAAAAAAAAAAAAAAull;
+        int p, q;
+        unsigned cr;
+        if (kk < c.ne * c.cE) {
+            unsigned t = kk / c.cE;
+            cr = kk % c.cE;
+            const unsigned tE = (unsigned)(c.a * (c.a - 1) / 2), tO = (unsigned)(c.b * (c.b - 1) / 2);
+            int i, j;
+            if (t < tE) {
+                tri_unrank(t, c.a, i, j);
+                p = nth_set64(E, i); q = nth_set64(E, j);
+            } else if (t < tE + tO) {
+                tri_unrank(t - tE, c.b, i, j);
+                p = nth_set64(O, i); q = nth_set64(O, j);
+            } else {
+                p = q = nth_set64(c.ge2, (int)(t - tE - tO));
+            }
+        } else {
+            unsigned k2 = kk - c.ne * c.cE;
+            unsigned t = k2 / c.cO;
+            cr = k2 % c.cO;
+            p = nth_set64(E, (int)(t / (unsigned)c.b));
+            q = nth_set64(O, (int)(t % (unsigned)c.b));
+        }
+        const int P = (p + q) % M;
+        const int lo = p < q ? p : q;
+        const int half = P / 2;
+        const unsigned rank_id = lo <= half ? (unsigned)lo : (unsigned)(half + 1 + (lo - P - 1));
+        if (cr >= rank_id) ++cr;
+        const int r = (int)cr <= half ? (int)cr : P + 1 + ((int)cr - half - 1);
+        const int s = r <= P ? P - r : P + M - r;
+        const long long np = mode_occ(key, p), nq = mode_occ(key, q);
+        const long long A = np * (nq - (p == q ? 1 : 0));
+        K k1 = remove_boson(remove_boson(key, p), q);
+        const long long nr = mode_occ(k1, r), ns = mode_occ(k1, s);
+        const long long B = (nr + 1) * (ns + 1 + (r == s ? 1 : 0));
+        const int F = (p != q ? 2 : 1) * (r != s ? 2 : 1);
+        val = (pm.g * (double)F) * sqrt((double)(A * B));
+        return add_boson(add_boson(k1, r), s);
+    }
+};
+
+template <> struct Model<FQ_KIND_REAL_1D> : RealModel<FQ_KIND_REAL_1D> {};
+template <> struct Model<FQ_KIND_REAL_2D> : RealModel<FQ_KIND_REAL_2D> {};
+template <> struct Model<FQ_KIND_MOM_1D> : MomModel {};
+
+}  // namespace fq

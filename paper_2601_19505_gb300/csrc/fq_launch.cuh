@@ -1,0 +1,114 @@
+// fq_launch.cuh -- launcher definitions for one (address, amplitude) pair;
+// included by the fq_inst_*.cu translation units only.
+#pragma once
+
+#include "fq_kernels.cuh"
+#include "fq_launch.h"
+
+namespace fq {
+
+template <class K, int AMP, int KIND> struct Launch {
+    typedef typename AmpT<AMP>::A A;
+    typedef typename AmpT<AMP>::S S;
+    typedef typename AmpT<AMP>::ACC ACC;
+
+    static void spawn(const LaunchCfg& c, const RunDesc* d, const unsigned* sr, unsigned G,
+                      cudaStream_t s) {
+        if (c.spawn_block == 512)
+            k_spawn<K, AMP, KIND, 512, 2><<<c.spawn_grid, 512, 0, s>>>(d, sr, G);
+        else
+            k_spawn<K, AMP, KIND, 256, 4><<<c.spawn_grid, 256, 0, s>>>(d, sr, G);
+    }
+    static void merge(const LaunchCfg& c, const RunDesc* d, const unsigned* sr, unsigned G,
+                      cudaStream_t s) {
+        const size_t smem = (size_t)c.slots * (sizeof(K) + sizeof(ACC));
+        if (c.merge_block == 512)
+            k_merge<K, AMP, KIND, 512><<<c.merge_grid, 512, smem, s>>>(d, sr, G, c.slots);
+        else
+            k_merge<K, AMP, KIND, 256><<<c.merge_grid, 256, smem, s>>>(d, sr, G, c.slots);
+    }
+    static cudaError_t prepare(size_t smem) {
+        cudaError_t e = cudaFuncSetAttribute(k_merge<K, AMP, KIND, 512>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(k_merge<K, AMP, KIND, 256>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    static int spawn_occupancy(int block) {
+        int n = 0;
+        if (block == 512)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spawn<K, AMP, KIND, 512, 2>, 512, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spawn<K, AMP, KIND, 256, 4>, 256, 0);
+        return n;
+    }
+    static int merge_occupancy(int block, size_t smem) {
+        int n = 0;
+        if (block == 512)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_merge<K, AMP, KIND, 512>, 512, smem);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_merge<K, AMP, KIND, 256>, 256, smem);
+        return n;
+    }
+    static void seed(const RunDesc* d, const void* keys, const double* amps, size_t n,
+                     cudaStream_t s) {
+        if (!n) return;
+        k_seed<K, AMP><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d, (const K*)keys, amps, n);
+    }
+    static void gather_vec(const void* keys, const void* amps, unsigned cap, const unsigned* cnt,
+                           const unsigned* off, unsigned B, void* okeys, double* ovals,
+                           cudaStream_t s) {
+        k_gather<K, A><<<B < 4096 ? B : 4096, 256, 0, s>>>((const K*)keys, (const A*)amps, cap, cnt,
+                                                           off, B, (K*)okeys, ovals);
+    }
+    static void gather_spawns(const void* keys, const void* vals, unsigned cap, const unsigned* cnt,
+                              const unsigned* off, unsigned B, void* okeys, double* ovals,
+                              cudaStream_t s) {
+        k_gather<K, S><<<B < 4096 ? B : 4096, 256, 0, s>>>((const K*)keys, (const S*)vals, cap, cnt,
+                                                           off, B, (K*)okeys, ovals);
+    }
+    static void column(const ModelParams& mp, const void* key, void* dest, double* val,
+                       unsigned cap, double* diag, unsigned* m, cudaStream_t s) {
+        k_column<K, KIND><<<1, 1, 0, s>>>(mp, *(const K*)key, (K*)dest, val, cap, diag, m);
+    }
+    static void ref_count(const ModelParams& mp, const void* refs, int n, unsigned* m,
+                          cudaStream_t s) {
+        k_ref_count<K, KIND><<<(n + 63) / 64, 64, 0, s>>>(mp, (const K*)refs, n, m);
+    }
+    static void ref_terms(const ModelParams& mp, const void* refs, const double* y, int n,
+                          const unsigned* off, void* tkeys, double* th, double* tv,
+                          unsigned* tseg, int log2B, cudaStream_t s) {
+        k_ref_terms<K, KIND><<<(n + 63) / 64, 64, 0, s>>>(mp, (const K*)refs, y, n, off,
+                                                          (K*)tkeys, th, tv, tseg, log2B);
+    }
+    static KernelSet make() {
+        KernelSet k;
+        k.key_bytes = sizeof(K);
+        k.amp_bytes = sizeof(A);
+        k.spawn_bytes = sizeof(S);
+        k.acc_bytes = sizeof(ACC);
+        k.spawn = spawn;
+        k.merge = merge;
+        k.prepare = prepare;
+        k.spawn_occupancy = spawn_occupancy;
+        k.merge_occupancy = merge_occupancy;
+        k.seed = seed;
+        k.gather_vec = gather_vec;
+        k.gather_spawns = gather_spawns;
+        k.column = column;
+        k.ref_count = ref_count;
+        k.ref_terms = ref_terms;
+        return k;
+    }
+};
+
+}  // namespace fq
+
+#define FQ_INSTANTIATE(NAME, KEY, AMP)                                    \
+    namespace fq {                                                        \
+    void NAME(KernelSet* out) {                                           \
+        out[0] = Launch<KEY, AMP, FQ_KIND_REAL_1D>::make();               \
+        out[1] = Launch<KEY, AMP, FQ_KIND_REAL_2D>::make();               \
+        out[2] = Launch<KEY, AMP, FQ_KIND_MOM_1D>::make();                \
+    }                                                                     \
+    }

@@ -1,0 +1,36 @@
+// fq_launch.h -- host-side table of kernel launchers, one entry per
+// (address width, amplitude type, Hamiltonian kind).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fq_shared.h"
+
+namespace fq {
+
+struct KernelSet {
+    size_t key_bytes, amp_bytes, spawn_bytes, acc_bytes;
+    void (*spawn)(const LaunchCfg&, const RunDesc*, const unsigned*, unsigned, cudaStream_t);
+    void (*merge)(const LaunchCfg&, const RunDesc*, const unsigned*, unsigned, cudaStream_t);
+    cudaError_t (*prepare)(size_t merge_smem);
+    int (*spawn_occupancy)(int block);
+    int (*merge_occupancy)(int block, size_t smem);
+    void (*seed)(const RunDesc*, const void*, const double*, size_t, cudaStream_t);
+    void (*gather_vec)(const void* keys, const void* amps, unsigned cap, const unsigned* cnt,
+                       const unsigned* off, unsigned B, void* okeys, double* ovals, cudaStream_t);
+    void (*gather_spawns)(const void* keys, const void* vals, unsigned cap, const unsigned* cnt,
+                          const unsigned* off, unsigned B, void* okeys, double* ovals, cudaStream_t);
+    void (*column)(const ModelParams&, const void* key, void* dest, double* val, unsigned cap,
+                   double* diag, unsigned* m, cudaStream_t);
+    void (*ref_count)(const ModelParams&, const void* refs, int n, unsigned* m, cudaStream_t);
+    void (*ref_terms)(const ModelParams&, const void* refs, const double* y, int n,
+                      const unsigned* off, void* tkeys, double* th, double* tv, unsigned* tseg,
+                      int log2B, cudaStream_t);
+};
+
+// kw = 64-bit words per address (1 or 2), amp = FQ_AMP_*, kind = FQ_KIND_*
+const KernelSet* kernel_set(int kw, int amp, int kind);
+
+void launch_shift(const RunDesc* runs, int nruns, cudaStream_t s);
+
+}  // namespace fq

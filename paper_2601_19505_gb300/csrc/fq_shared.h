@@ -1,0 +1,94 @@
+// fq_shared.h -- plain structs shared by the host driver (fq_api.cu) and the
+// kernels: model parameters, per-run device state, the per-run descriptor
+// the batched kernels read, and launch shapes.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#define FQ_KIND_REAL_1D 1
+#define FQ_KIND_REAL_2D 2
+#define FQ_KIND_MOM_1D 3
+
+// amplitude representation
+#define FQ_AMP_INT 0  // int64 amplitudes, int32 spawns
+#define FQ_AMP_F64 1  // double amplitudes and spawns
+#define FQ_AMP_F32 2  // float amplitudes and spawns, FP64 sums
+
+// device-side error bits (RunState::err)
+#define FQ_DERR_SPAWN_CAP 1u
+#define FQ_DERR_VEC_CAP 2u
+#define FQ_DERR_TABLE 4u
+#define FQ_DERR_EMPTY 8u
+#define FQ_DERR_TIMEOUT 16u
+
+#define FQ_MAX_MOM_MODES 64
+#define FQ_HIST_CAP 65536u
+
+namespace fq {
+
+struct ModelParams {
+    int kind, M, N, Lx, Ly, nbits;
+    double t, u;
+    double g;                        // u / (2M), momentum space
+    double eps[FQ_MAX_MOM_MODES];    // momentum-space single-particle energies
+};
+
+// One row of the time series; layout identical to fq_stats in fciqmc.h.
+struct StatsRow {
+    long long step, len, exact_steps, inexact_steps, n_spawns;
+    double shift, norm, hproj, vproj;
+};
+
+// Mutable per-run state in device memory.  The kernels of step n read
+// shift/norm/step/cur; the shift kernel writes the next values.
+struct RunState {
+    double shift;      // S^(n)
+    double norm;       // N^(n) = ||c^(n)||_1
+    double dt, target, zeta, xi;
+    long long step;    // n
+    long long len;     // occupied entries of c^(n)
+    int cur;           // vector buffer holding c^(n)
+    unsigned err;      // FQ_DERR_* bits; a set bit freezes the run
+    unsigned long long n_exact, n_inexact, n_spawns;  // step in flight
+    unsigned long long hist_head;                     // rows written
+    double last_hproj, last_vproj;
+    long long last_exact, last_inexact, last_spawns;
+};
+
+// Everything a kernel needs to process one run's segments.  Lives in a
+// device array, one entry per run of a batch.
+struct RunDesc {
+    ModelParams mp;
+    int mode_det;       // deterministic limit: every column exact, no compression
+    double theta, t_rel;
+    unsigned key_x, key_y;   // Philox key
+    int log2B;
+    unsigned B, seg_base, Cv, Cs;
+    void* vkeys[2];
+    void* vamps[2];
+    unsigned* vcount[2];
+    void* skeys;
+    void* samps;
+    unsigned* sfill;
+    RunState* st;
+    StatsRow* hist;
+    const void* ref_keys;     // reference terms sorted by segment
+    const double* ref_h;      // y_r H_{r,j}
+    const double* ref_v;      // y_r on the reference address itself, else 0
+    const unsigned* ref_off;  // B + 1 offsets into the reference terms
+    double* part_norm;        // per-segment partial sums (length B)
+    double* part_h;
+    double* part_v;
+    unsigned long long* part_len;
+};
+
+struct LaunchCfg {
+    int spawn_block;      // threads per spawn block (256 or 512)
+    int spawn_grid;       // persistent spawn blocks
+    int merge_block;      // threads per merge block
+    int merge_grid;       // persistent merge blocks
+    unsigned slots;       // on-chip table slots per merge block (power of 2)
+};
+
+}  // namespace fq

@@ -1,0 +1,285 @@
+"""Python objects over the C ABI of libfciqmc (include/fciqmc.h).
+
+Every call forwards to the function of the same name in the C ABI; nothing
+here computes any part of the step.  Device memory comes from PyTorch's
+caching allocator and work is queued on PyTorch's current CUDA stream unless
+told otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+
+BH_REAL_1D, BH_REAL_2D, BH_MOM_1D = 1, 2, 3
+MODE_INT, MODE_REAL64, MODE_REAL32, MODE_DETERMINISTIC = 0, 1, 2, 3
+ANN_AUTO, ANN_HASH = 0, 2
+
+KEY_DTYPE = np.dtype([("lo", "<u8"), ("hi", "<u8")])
+STATS_DTYPE = np.dtype([("step", "<i8"), ("len", "<i8"), ("exact_steps", "<i8"),
+                        ("inexact_steps", "<i8"), ("n_spawns", "<i8"), ("shift", "<f8"),
+                        ("norm", "<f8"), ("hproj", "<f8"), ("vproj", "<f8")])
+
+
+class FqError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = L.load().fq_strerror(code).decode()
+        super().__init__("%s: %s (%d)" % (what, msg, code))
+
+
+def _check(code: int, what: str):
+    if code:
+        raise FqError(code, what)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def version() -> str:
+    return L.load().fq_version().decode()
+
+
+def keys_from_ints(keys) -> np.ndarray:
+    out = np.zeros(len(keys), dtype=KEY_DTYPE)
+    for i, k in enumerate(keys):
+        k = int(k)
+        out[i] = (k & 0xFFFFFFFFFFFFFFFF, k >> 64)
+    return out
+
+
+def keys_to_ints(keys: np.ndarray):
+    return [int(k["lo"]) | (int(k["hi"]) << 64) for k in keys]
+
+
+def _as_keys(keys) -> np.ndarray:
+    if isinstance(keys, np.ndarray) and keys.dtype == KEY_DTYPE:
+        return np.ascontiguousarray(keys)
+    if isinstance(keys, np.ndarray) and keys.dtype.names == ("lo", "hi"):
+        return np.ascontiguousarray(keys).view(KEY_DTYPE)
+    return keys_from_ints(keys)
+
+
+def default_params(**kw) -> L.FqParams:
+    """fq_params_default, then the given fields; setting zeta alone also sets
+    xi = zeta^2 / 4."""
+    p = L.FqParams()
+    _check(L.load().fq_params_default(C.byref(p)), "fq_params_default")
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    if "zeta" in kw and "xi" not in kw:
+        p.xi = p.zeta ** 2 / 4
+    return p
+
+
+class Hamiltonian:
+    """fq_ham_create(kind, Lx, Ly, N, t, u)."""
+
+    def __init__(self, kind: int, Lx: int, Ly: int, N: int, t: float, u: float):
+        self._lib = L.load()
+        h = C.c_void_p()
+        _check(self._lib.fq_ham_create(C.byref(h), kind, Lx, Ly, N, t, u), "fq_ham_create")
+        self.h = h
+        self.kind, self.Lx, self.Ly, self.N, self.t, self.u = kind, Lx, Ly, N, t, u
+        M, nb, kw = C.c_int(), C.c_int(), C.c_int()
+        self._lib.fq_ham_info(h, C.byref(M), C.byref(nb), C.byref(kw))
+        self.M, self.nbits, self.key_words = M.value, nb.value, kw.value
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self._lib.fq_ham_destroy(self.h)
+            self.h = None
+
+    def dimension(self) -> float:
+        d = C.c_double()
+        _check(self._lib.fq_ham_dimension(self.h, C.byref(d)), "fq_ham_dimension")
+        return d.value
+
+    def starting_address(self) -> int:
+        k = L.FqKey()
+        _check(self._lib.fq_ham_starting_address(self.h, C.byref(k)), "fq_ham_starting_address")
+        return k.lo | (k.hi << 64)
+
+    def encode(self, occ) -> int:
+        o = np.ascontiguousarray(occ, dtype=np.uint8)
+        k = L.FqKey()
+        _check(self._lib.fq_encode(self.h, _ptr(o), C.byref(k)), "fq_encode")
+        return k.lo | (k.hi << 64)
+
+    def decode(self, key) -> np.ndarray:
+        o = np.zeros(self.M, dtype=np.uint8)
+        k = int(key)
+        _check(self._lib.fq_decode(self.h, L.FqKey(k & 0xFFFFFFFFFFFFFFFF, k >> 64), _ptr(o)),
+               "fq_decode")
+        return o
+
+    def column(self, key, cap: int = 1 << 16):
+        """(diagonal, [destination ints], values) from the device code."""
+        k = int(key)
+        dest = np.zeros(cap, dtype=KEY_DTYPE)
+        val = np.zeros(cap)
+        d, m = C.c_double(), C.c_size_t()
+        _check(self._lib.fq_ham_column(self.h, L.FqKey(k & 0xFFFFFFFFFFFFFFFF, k >> 64),
+                                       C.byref(d), _ptr(dest), _ptr(val), cap, C.byref(m)),
+               "fq_ham_column")
+        n = min(m.value, cap)
+        return d.value, keys_to_ints(dest[:n]), val[:n].copy()
+
+
+class _TorchAllocator:
+    """Routes device allocations through torch.cuda's caching allocator."""
+
+    def __init__(self):
+        import torch
+
+        self.torch = torch
+        self.device = torch.cuda.current_device()
+        self._alloc = L.ALLOC_FN(self.alloc)
+        self._free = L.FREE_FN(self.free)
+        self.struct = L.FqAllocator(None, self._alloc, self._free)
+
+    def alloc(self, ctx, nbytes, stream):
+        try:
+            return self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device,
+                                                           int(stream or 0))
+        except Exception:  # noqa: BLE001 - the C side reports FQ_ERR_NOMEM
+            return None
+
+    def free(self, ctx, ptr, nbytes, stream):
+        self.torch.cuda.caching_allocator_delete(int(ptr))
+
+
+def _current_stream():
+    import torch
+
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Run:
+    """fq_run_create(h, params, stream, allocator)."""
+
+    def __init__(self, ham: Hamiltonian, params: L.FqParams | None = None, stream=None,
+                 torch_allocator: bool = True):
+        self._lib = L.load()
+        self.ham = ham
+        self.params = params if params is not None else default_params()
+        self.stream = _current_stream() if stream is None else int(stream)
+        self._alloc = _TorchAllocator() if torch_allocator else None
+        r = C.c_void_p()
+        _check(self._lib.fq_run_create(C.byref(r), ham.h, C.byref(self.params),
+                                       C.c_void_p(self.stream),
+                                       C.byref(self._alloc.struct) if self._alloc else None),
+               "fq_run_create")
+        self.r = r
+
+    def close(self):
+        if getattr(self, "r", None):
+            self._lib.fq_run_destroy(self.r)
+            self.r = None
+
+    def __del__(self):
+        self.close()
+
+    def seed(self, keys, amps, shift: float, step: int = 0):
+        k = _as_keys(keys)
+        a = np.ascontiguousarray(amps, dtype=np.float64)
+        _check(self._lib.fq_run_seed(self.r, _ptr(k), _ptr(a), len(a), float(shift), int(step)),
+               "fq_run_seed")
+
+    def seed_default(self, weight: float = 10.0):
+        _check(self._lib.fq_run_seed_default(self.r, float(weight)), "fq_run_seed_default")
+
+    def set_reference(self, keys, y):
+        k = _as_keys(keys)
+        a = np.ascontiguousarray(y, dtype=np.float64)
+        _check(self._lib.fq_run_set_reference(self.r, _ptr(k), _ptr(a), len(a)),
+               "fq_run_set_reference")
+
+    def set_dt(self, dt: float):
+        _check(self._lib.fq_run_set_dt(self.r, float(dt)), "fq_run_set_dt")
+
+    def set_shift(self, s: float):
+        _check(self._lib.fq_run_set_shift(self.r, float(s)), "fq_run_set_shift")
+
+    def set_target(self, t: float):
+        _check(self._lib.fq_run_set_target(self.r, float(t)), "fq_run_set_target")
+
+    def step(self, n: int = 1):
+        _check(self._lib.fq_run_step(self.r, int(n)), "fq_run_step")
+
+    def sync(self) -> int:
+        return self._lib.fq_run_sync(self.r)
+
+    def stats(self) -> dict:
+        s = L.FqStats()
+        _check(self._lib.fq_run_stats(self.r, C.byref(s)), "fq_run_stats")
+        return {f: getattr(s, f) for f, _ in L.FqStats._fields_}
+
+    def history(self, cap: int = 1 << 16) -> np.ndarray:
+        out = np.zeros(cap, dtype=STATS_DTYPE)
+        n = C.c_size_t()
+        _check(self._lib.fq_run_history(self.r, _ptr(out), cap, C.byref(n)), "fq_run_history")
+        return out[: n.value].copy()
+
+    def export(self):
+        n = C.c_size_t()
+        _check(self._lib.fq_run_export(self.r, None, None, 0, C.byref(n)), "fq_run_export")
+        cap = n.value
+        k = np.zeros(max(cap, 1), dtype=KEY_DTYPE)
+        a = np.zeros(max(cap, 1))
+        _check(self._lib.fq_run_export(self.r, _ptr(k), _ptr(a), cap, C.byref(n)), "fq_run_export")
+        return k[: n.value].copy(), a[: n.value].copy()
+
+    def spawns(self, cap: int | None = None):
+        n = C.c_size_t()
+        if cap is None:
+            cap = 1 << 22
+        d = np.zeros(cap, dtype=KEY_DTYPE)
+        v = np.zeros(cap)
+        _check(self._lib.fq_run_spawns(self.r, _ptr(d), _ptr(v), cap, C.byref(n)), "fq_run_spawns")
+        if n.value > cap:
+            raise FqError(-3, "fq_run_spawns: %d spawns exceed the buffer" % n.value)
+        return d[: n.value].copy(), v[: n.value].copy()
+
+    def autotune(self, steps: int = 3):
+        _check(self._lib.fq_run_autotune(self.r, int(steps)), "fq_run_autotune")
+
+    def profile(self, n: int):
+        """Mean ms per step of (spawn, merge, shift) over n eagerly launched steps."""
+        ms = (C.c_float * 3)()
+        _check(self._lib.fq_run_profile(self.r, int(n), ms), "fq_run_profile")
+        return tuple(float(x) for x in ms)
+
+
+class Batch:
+    """fq_batch_create(runs): the runs step together, one launch per kernel."""
+
+    def __init__(self, runs):
+        self._lib = L.load()
+        self.runs = list(runs)
+        arr = (C.c_void_p * len(self.runs))(*[r.r.value for r in self.runs])
+        b = C.c_void_p()
+        _check(self._lib.fq_batch_create(C.byref(b), arr, len(self.runs)), "fq_batch_create")
+        self.b = b
+
+    def close(self):
+        if getattr(self, "b", None):
+            self._lib.fq_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        self.close()
+
+    def step(self, n: int = 1):
+        _check(self._lib.fq_batch_step(self.b, int(n)), "fq_batch_step")
+
+    def sync(self):
+        _check(self._lib.fq_batch_sync(self.b), "fq_batch_sync")
+
+    def autotune(self, steps: int = 3):
+        _check(self._lib.fq_batch_autotune(self.b, int(steps)), "fq_batch_autotune")

@@ -1,0 +1,168 @@
+"""GPU path vs CPU oracle, through the C ABI (needs a GB300).
+
+Bars (the method's own): addresses, occupied sets and integer-walker runs
+bit-exact; FP64 amplitudes within 1e-12 relative over the first 50 steps;
+FP32 amplitudes within 1e-6 relative (a changed summation order may move one
+FP32 rounding by an ulp); spawn lists bit-exact (draws are keyed by content,
+so order does not matter).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_helpers import assert_same_vector, fq, pair, runs, seeded_vector, sorted_pairs
+
+pytestmark = pytest.mark.gpu
+
+MODELS = [
+    (O.REAL_1D, 6, 1, 6, 1.0, 6.0),
+    (O.REAL_1D, 20, 1, 20, 1.0, 2.0),
+    (O.REAL_2D, 4, 3, 9, 1.0, 3.0),
+    (O.REAL_2D, 8, 8, 64, 1.0, 8.0),      # 127-bit addresses
+    (O.MOM_1D, 8, 1, 8, 1.0, 4.0),
+    (O.MOM_1D, 32, 1, 32, 1.0, 4.0),      # 63-bit addresses
+    (O.MOM_1D, 7, 1, 9, 1.0, 2.0),        # odd M
+    (O.REAL_1D, 70, 1, 30, 1.0, 2.0),     # 99-bit, real space
+]
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_column_bit_exact(model):
+    h, m = pair(*model)
+    rng = np.random.default_rng(3)
+    keys = [m.start()] + seeded_vector(m, 60, 11)[0]
+    for k in keys[:61]:
+        d, dk, dv = h.column(k)
+        ok, ov = m.column(k)
+        assert d == m.diagonal(k)
+        assert dk == ok
+        assert np.array_equal(dv, ov)
+    del rng
+
+
+@pytest.mark.parametrize("mode", ["REAL64", "REAL32", "INT"])
+@pytest.mark.parametrize("model", MODELS)
+def test_spawn_list_bit_exact(model, mode):
+    h, m = pair(*model)
+    mcode = {"REAL64": 1, "REAL32": 2, "INT": 0}[mode]
+    keys, amps = seeded_vector(m, 3000, 5, mode=mode)
+    g, o = runs(h, m, mode=mcode, dt=0.003, target=1e5, seed=42, run_id=3,
+                capacity_vec=20000, capacity_spawn=400000)
+    g.seed(fq().keys_from_ints(keys), amps, -1.5, step=17)
+    o.seed(keys, amps, -1.5, step=17)
+    o.record_spawns()
+    gd, gv = g.spawns()
+    o.step(1)
+    od, osrc, ov = o.spawns()
+    assert len(gd) == len(od)
+    gd, gv = sorted_pairs(gd, gv)
+    od, ov = sorted_pairs(od, ov)
+    assert np.array_equal(gd["lo"], od["lo"]) and np.array_equal(gd["hi"], od["hi"])
+    assert np.array_equal(gv, ov)
+    # the spawning stage leaves the run untouched
+    g.step(1)
+    assert_same_vector(g.export(), o.export(), rtol=1e-12 if mode != "REAL32" else 1e-6,
+                       what="after one step")
+
+
+@pytest.mark.parametrize("mode", ["REAL64", "REAL32", "INT", "DETERMINISTIC"])
+@pytest.mark.parametrize("model", [MODELS[0], MODELS[2], MODELS[4], MODELS[6]])
+def test_fifty_steps_from_default_start(model, mode):
+    h, m = pair(*model)
+    mcode = {"REAL64": 1, "REAL32": 2, "INT": 0, "DETERMINISTIC": 3}[mode]
+    dt = 0.01 if mode != "INT" else 0.002
+    g, o = runs(h, m, mode=mcode, dt=dt, target=2000.0, seed=9)
+    g.seed_default(10.0)
+    s = m.start()
+    o.seed([s], [10.0], m.diagonal(s), 0)
+    o.set_reference([s], [10.0])
+    rtol = {"REAL64": 1e-12, "REAL32": 1e-6, "INT": 0.0, "DETERMINISTIC": 1e-12}[mode]
+    for block in range(5):
+        g.step(10)
+        o.step(10)
+        if mode == "DETERMINISTIC":
+            # no compression: amplitudes far below the vector's scale come out
+            # of cancelling sums, whose rounding depends on the summation
+            # order; the bound is relative to the vector's largest amplitude
+            (gk, ga), (ok, oa) = g.export(), o.export()
+            assert np.array_equal(gk, ok)
+            assert np.max(np.abs(ga - oa)) <= 1e-12 * np.max(np.abs(oa))
+            continue
+        assert_same_vector(g.export(), o.export(), rtol=rtol, what="step %d" % (10 * block + 10))
+    gh, oh = g.history(), o.history()
+    assert len(gh) == 50
+    for f in ("step", "len", "exact_steps", "inexact_steps", "n_spawns"):
+        assert np.array_equal(gh[f], oh[f]), f
+    tol = 1e-12 if mode != "REAL32" else 1e-6
+    for f in ("shift", "norm", "hproj", "vproj"):
+        assert np.allclose(gh[f], oh[f], rtol=tol, atol=tol), f
+
+
+@pytest.mark.parametrize("mode", ["REAL64", "REAL32", "INT"])
+@pytest.mark.parametrize("model", [MODELS[1], MODELS[3], MODELS[5]])
+def test_large_seeded_vector_steps(model, mode):
+    """A 20k-entry seeded vector (many segments, ragged segment fills) for
+    three steps."""
+    h, m = pair(*model)
+    mcode = {"REAL64": 1, "REAL32": 2, "INT": 0}[mode]
+    keys, amps = seeded_vector(m, 20000, 21, mode=mode)
+    g, o = runs(h, m, mode=mcode, dt=0.001, target=float(np.abs(amps).sum()), seed=5,
+                capacity_vec=200000, capacity_spawn=2000000)
+    g.seed(fq().keys_from_ints(keys), amps, -2.0, step=100)
+    o.seed(keys, amps, -2.0, step=100)
+    refs = keys[:5]
+    g.set_reference(fq().keys_from_ints(refs), [1.0, 2.0, 3.0, -1.0, 0.5])
+    o.set_reference(refs, [1.0, 2.0, 3.0, -1.0, 0.5])
+    rtol = {"REAL64": 1e-12, "REAL32": 1e-6, "INT": 0.0}[mode]
+    for s in range(3):
+        g.step(1)
+        o.step(1)
+        assert_same_vector(g.export(), o.export(), rtol=rtol, what="step %d" % s)
+    gh, oh = g.history(), o.history()
+    for f in ("len", "exact_steps", "inexact_steps", "n_spawns"):
+        assert np.array_equal(gh[f], oh[f]), f
+    tol = 1e-11 if mode != "REAL32" else 1e-6
+    for f in ("shift", "norm", "hproj", "vproj"):
+        assert np.allclose(gh[f], oh[f], rtol=tol, atol=tol), f
+
+
+def test_empty_vector_and_population_death():
+    h, m = pair(*MODELS[0])
+    g, o = runs(h, m, seed=2)
+    g.seed([], [], 0.0)
+    st = g.stats()
+    assert st["len"] == 0 and st["norm"] == 0.0
+    # one boson in two momentum modes has no off-diagonal elements; with
+    # S = H_ii - 1/dt the diagonal factor is exactly 0 and the walker dies
+    h1 = fq().Hamiltonian(fq().BH_MOM_1D, 2, 1, 1, 1.0, 1.0)
+    r = fq().Run(h1, fq().default_params(dt=0.01))
+    s = h1.starting_address()
+    diag = h1.column(s)[0]
+    r.seed([s], [3.0], diag - 100.0)
+    r.step(1)
+    with pytest.raises(fq().FqError) as e:
+        r.stats()
+    assert e.value.code == -5
+    # rolled back: the run is still at step 0 with its vector, and continues
+    assert r.stats()["step"] == 0
+    r.set_shift(diag)
+    r.step(1)
+    st = r.stats()
+    assert st["step"] == 1 and st["len"] == 1 and st["norm"] == 3.0
+
+
+def test_capacity_overflow_rolls_back():
+    h, m = pair(*MODELS[1])
+    g = fq().Run(h, fq().default_params(dt=0.001, target=1e6, capacity_vec=4096,
+                                        capacity_spawn=4096))
+    g.seed_default(10.0)
+    rc = 0
+    for _ in range(400):
+        g.step(10)
+        rc = g.sync()
+        if rc:
+            break
+    assert rc == -3
+    st = g.stats()
+    k, a = g.export()
+    assert len(k) == st["len"] and np.isclose(np.abs(a).sum(), st["norm"], rtol=1e-12)
