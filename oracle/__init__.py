@@ -109,6 +109,8 @@ def lib():
         L.or_run_spawns.restype = C.c_long
         L.or_run_spawns.argtypes = [vp, C.c_void_p, C.c_void_p, C.c_void_p, C.c_long]
         L.or_point.argtypes = [vp, kp, dp, dp]
+        L.or_exact_norm_of.restype = C.c_double
+        L.or_exact_norm_of.argtypes = [C.c_void_p, C.c_long, C.c_double, C.c_int]
         L.or_shift_update.restype = C.c_double
         L.or_shift_update.argtypes = [C.c_double] * 7
         L.or_build_sparse.restype = C.c_long
@@ -152,6 +154,12 @@ def philox4x32_10(ctr, key) -> tuple:
     o = np.zeros(4, dtype=np.uint32)
     lib().or_philox(_ptr(c), _ptr(k), _ptr(o))
     return tuple(int(x) for x in o)
+
+
+def exact_norm(amps, threshold: float = 1.0, mode: int = MODE_REAL64) -> float:
+    """The oracle's one-norm of a vector with these amplitudes."""
+    a = np.ascontiguousarray(amps, dtype=np.float64)
+    return lib().or_exact_norm_of(_ptr(a), len(a), threshold, mode)
 
 
 def shift_update(S, N0, N1, dt, zeta, xi, target) -> float:

@@ -241,7 +241,7 @@ typedef struct { okey key; double val; } colent;
  *   4. (even mode, odd mode) pairs, even-mode-major.
  * For each, the created pairs follow in ascending r over
  * r = 0..M-1, s = (p + k - r) mod M, r <= s, skipping the identity.  Value
- * (u/2M) F sqrt(A B) with F = (2 if p != k else 1)(2 if r != s else 1),
+ * ((u/2M) F) sqrt(A) sqrt(B) with F = (2 if p != k else 1)(2 if r != s else 1),
  * A = n_p (n_k - [p == k]), B = (m_r + 1)(m_s + 1 + [r == s]),
  * m = n - e_p - e_k. */
 static long column(const or_model *md, const uint8_t *occ, colent *ent, long cap) {
@@ -293,7 +293,7 @@ static long column(const or_model *md, const uint8_t *occ, colent *ent, long cap
                 d[r]++; d[s]++;
                 int F = (p != k ? 2 : 1) * (r != s ? 2 : 1);
                 ent[m].key = encode_occ(md, d);
-                ent[m].val = (g * (double)F) * sqrt((double)(A * B));
+                ent[m].val = ((g * (double)F) * sqrt((double)A)) * sqrt((double)B);
             }
             m++;
         }
@@ -489,12 +489,13 @@ static void source_contribs(const or_model *md, const or_params *pr, uint32_t st
          * stochastically to an integer. */
         (*n_inexact)++;
         int64_t nat = (int64_t)fabs(c);
+        double dtm = dt * (double)m;
         for (int64_t a = 0; a < nat && m > 0; ++a) {
             uint32_t w[4];
             draw(pr, step, (uint32_t)a, h, w);
             uint32_t k = pick(w, (uint32_t)m);
             double hv = col[k].val;
-            double p = (dt * fabs(hv)) * (double)m;
+            double p = fabs(hv) * dtm;
             double fl = floor(p);
             int64_t cnt = (int64_t)fl + (uniform53(w) < p - fl ? 1 : 0);
             if (cnt) {
@@ -515,11 +516,49 @@ static void source_contribs(const or_model *md, const or_params *pr, uint32_t st
 
     /* Exact column when |c_i| t_rel >= m_i (Sec. 7.1); always in the
      * deterministic limit. */
+    if (pr->mode == OR_REAL32) {
+        /* FP32 amplitudes: every per-entry product in FP32; the diagonal term
+         * is c + c delta with delta = dt (S - H_ii) rounded once to FP32, so
+         * that the factor 1 + delta carries no rounding bias of its own. */
+        const float cf = (float)c, dtf = (float)dt;
+        const float delta = (float)(dt * (shift - hii));
+        int exact = fabs(c) * pr->t_rel >= (double)m;
+        if (exact) {
+            (*n_exact)++;
+            const float coef = (-dtf) * cf;
+            for (long k = 0; k < m; ++k) {
+                const float v = (float)col[k].val * coef;
+                push(out, col[k].key, key, (uint32_t)k, 1, (double)v);
+                (*n_spawns)++;
+            }
+        } else {
+            (*n_inexact)++;
+            const uint32_t n = (uint32_t)ceil(fabs(c));
+            const float coef = ((-dtf) * ((float)m / (float)n)) * cf;
+            for (uint32_t a = 0; a < n; ++a) {
+                uint32_t w[4];
+                draw(pr, step, a, h, w);
+                uint32_t k = pick(w, (uint32_t)m);
+                const float v = (float)col[k].val * coef;
+                push(out, col[k].key, key, a, 1, (double)v);
+                (*n_spawns)++;
+            }
+        }
+        const float d = cf + cf * delta;
+        push(out, key, key, 0, 0, (double)d);
+        free(col);
+        return;
+    }
+
+    /* Each spawn is H_ji coef with coef = -dt c_i (exact column) or
+     * -dt (m_i / n_i) c_i (n_i picks), the factors of Eq. column-compression
+     * multiplied in this order. */
     int exact = pr->mode == OR_DETERMINISTIC || fabs(c) * pr->t_rel >= (double)m;
     if (exact) {
         (*n_exact)++;
+        double coef = (-dt) * c;
         for (long k = 0; k < m; ++k) {
-            double v = (-(dt * col[k].val)) * c;
+            double v = col[k].val * coef;
             push(out, col[k].key, key, (uint32_t)k, 1, store_round(pr->mode, v));
             (*n_spawns)++;
         }
@@ -527,12 +566,12 @@ static void source_contribs(const or_model *md, const or_params *pr, uint32_t st
         (*n_inexact)++;
         double nd = ceil(fabs(c));
         uint32_t n = (uint32_t)nd;
-        double scale = (double)m / (double)n; /* m_i / n_i of Eq. column-compression */
+        double coef = ((-dt) * ((double)m / (double)n)) * c;
         for (uint32_t a = 0; a < n; ++a) {
             uint32_t w[4];
             draw(pr, step, a, h, w);
             uint32_t k = pick(w, (uint32_t)m);
-            double v = ((-(dt * col[k].val)) * scale) * c;
+            double v = col[k].val * coef;
             push(out, col[k].key, key, a, 1, store_round(pr->mode, v));
             (*n_spawns)++;
         }
@@ -557,6 +596,51 @@ static int compress(const or_model *md, const or_params *pr, uint32_t step, okey
         return 1;
     }
     return 0;
+}
+
+/* The one-norm ||c||_1 = sum_i |c_i|, evaluated exactly and rounded once to
+ * the nearest double.  After vector compression every stored |c_i| is at
+ * least theta (or an integer in integer mode), so each is an integer
+ * multiple of 2^q with q = ilogb(theta) - 52 (q = 0 for integer walkers): the
+ * sum is taken in 128-bit integers of that unit.  The deterministic limit has
+ * no such floor; there the sum is the plain sequential one. */
+static int norm_unit(const or_params *pr) {
+    if (pr->mode == OR_INT) return 0;
+    return ilogb(pr->threshold) - 52;
+}
+
+static double exact_norm(const or_run *r) {
+    if (r->pr.mode == OR_DETERMINISTIC) {
+        double s = 0.0;
+        for (long i = 0; i < r->n; ++i) s += fabs(r->vec[i].amp);
+        return s;
+    }
+    int q = norm_unit(&r->pr);
+    unsigned __int128 acc = 0;
+    for (long i = 0; i < r->n; ++i)
+        acc += (unsigned __int128)ldexp(fabs(r->vec[i].amp), -q);
+    /* round to nearest, ties to even: keep the top 64 bits, fold every bit
+     * below them into the lowest kept bit, convert (64 > 53 + 1 bits) */
+    uint64_t hi = (uint64_t)(acc >> 64), lo = (uint64_t)acc;
+    if (!hi) return ldexp((double)lo, q);
+    int lz = __builtin_clzll(hi);
+    int sh = 64 - lz;
+    uint64_t top = (hi << lz) | (lo >> sh);
+    if (lo & ((1ull << sh) - 1)) top |= 1u;
+    return ldexp((double)top, q + sh);
+}
+
+double or_exact_norm_of(const double *amps, long n, double threshold, int mode) {
+    or_run r;
+    memset(&r, 0, sizeof r);
+    r.pr.threshold = threshold;
+    r.pr.mode = mode;
+    entry *e = (entry *)malloc(sizeof(entry) * (size_t)(n > 0 ? n : 1));
+    for (long i = 0; i < n; ++i) { e[i].amp = amps[i]; e[i].key.lo = e[i].key.hi = 0; }
+    r.vec = e; r.n = n;
+    double s = exact_norm(&r);
+    free(e);
+    return s;
 }
 
 static double lookup(const or_run *r, okey k) {
@@ -698,7 +782,13 @@ static int one_step(or_run *r) {
     for (long i = 0; i < cl.n;) {
         long j = i;
         double w = 0.0;
-        while (j < cl.n && key_cmp(cl.c[j].dest, cl.c[i].dest) == 0) { w += cl.c[j].val; j++; }
+        float wf = 0.0f;
+        while (j < cl.n && key_cmp(cl.c[j].dest, cl.c[i].dest) == 0) {
+            w += cl.c[j].val;
+            wf += (float)cl.c[j].val;
+            j++;
+        }
+        if (r->pr.mode == OR_REAL32) w = (double)wf;
         double out;
         if (compress(&r->md, &r->pr, step, cl.c[i].dest, w, &out)) {
             nv[nn].key = cl.c[i].dest;
@@ -711,8 +801,7 @@ static int one_step(or_run *r) {
     free(r->vec);
     r->vec = nv; r->n = nn; r->cap = cl.n;
 
-    double norm = 0.0;
-    for (long i = 0; i < r->n; ++i) norm += fabs(r->vec[i].amp);
+    double norm = exact_norm(r);
     r->step = step;
     if (norm == 0.0) { r->norm = 0.0; return -5; }
     r->shift = or_shift_update(r->shift, r->norm, norm, r->pr.dt, r->pr.zeta, r->pr.xi,
@@ -796,7 +885,12 @@ int or_point(const void *p, const okey *jkey, double *pre, double *post) {
     cl.n = keep;
     qsort(cl.c, (size_t)cl.n, sizeof(contrib), cmp_contrib);
     double w = 0.0;
-    for (long i = 0; i < cl.n; ++i) w += cl.c[i].val;
+    float wf = 0.0f;
+    for (long i = 0; i < cl.n; ++i) {
+        w += cl.c[i].val;
+        wf += (float)cl.c[i].val;
+    }
+    if (r->pr.mode == OR_REAL32) w = (double)wf;
     free(cl.c);
     *pre = w;
     double out = 0.0;

@@ -113,6 +113,25 @@ def test_printed_shift_rows():
     assert abs(S - g["series"][0]["rows"][0][2]) > 0.5
 
 
+def test_norm_is_the_exact_sum_rounded_once():
+    """||c||_1 = sum |c_i| in exact arithmetic, rounded once to nearest."""
+    from fractions import Fraction
+    rng = np.random.default_rng(8)
+    for trial in range(30):
+        n = int(rng.integers(1, 5000))
+        mag = np.exp(rng.uniform(0, 30, size=n)) if trial % 3 else 1.0 + rng.exponential(3, n)
+        a = mag * rng.choice([-1, 1], size=n)
+        if trial % 2:
+            a = a.astype(np.float32).astype(np.float64)
+        exact = float(sum(Fraction(abs(float(x))) for x in a))
+        assert O.exact_norm(a, 1.0, O.MODE_REAL64) == exact
+        half = np.where(np.abs(a) < 0.5, 0.5, a)
+        exact = float(sum(Fraction(abs(float(x))) for x in half))
+        assert O.exact_norm(half, 0.5, O.MODE_REAL64) == exact
+    ints = rng.integers(-10**12, 10**12, size=1000).astype(np.float64)
+    assert O.exact_norm(ints, 1.0, O.MODE_INT) == float(sum(abs(int(x)) for x in ints))
+
+
 def test_exact_column_rule_and_counts():
     m = O.Model(O.REAL_1D, 6, 1, 6, 1.0, 6.0)
     s = m.start()                     # m_i = 12
