@@ -625,8 +625,9 @@ static double exact_norm(const or_run *r) {
     if (!hi) return ldexp((double)lo, q);
     int lz = __builtin_clzll(hi);
     int sh = 64 - lz;
-    uint64_t top = (hi << lz) | (lo >> sh);
-    if (lo & ((1ull << sh) - 1)) top |= 1u;
+    uint64_t top = sh == 64 ? hi : ((hi << lz) | (lo >> sh));
+    uint64_t rest = sh == 64 ? lo : (lo & ((1ull << sh) - 1));
+    if (rest) top |= 1u;
     return ldexp((double)top, q + sh);
 }
 

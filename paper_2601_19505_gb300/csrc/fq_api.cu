@@ -53,6 +53,17 @@ const KernelSet* kernel_set(int kw, int amp, int kind) {
 void launch_shift(const RunDesc* runs, int nruns, cudaStream_t s) {
     k_shift<256><<<nruns, 256, 0, s>>>(runs);
 }
+
+static void launch_factors(const RunDesc* runs, int nruns, cudaStream_t s) {
+    k_factors<<<nruns, 256, 0, s>>>(runs);
+}
+
+// tables of sqrt(k), hop values and m / n for a model (device memory)
+struct Tables {
+    double *sq, *hop, *r64;
+    float *hop32, *r32;
+    int kmax, mmax;
+};
 }  // namespace fq
 
 // ---------------------------------------------------------------------------
@@ -86,8 +97,14 @@ struct fq_run {
     void* skeys;
     void* samps;
     unsigned* sfill;
-    double *part_norm, *part_h, *part_v;
-    unsigned long long* part_len;
+    double *part_h, *part_v;
+    Tables tab;
+    int smax;
+    double* fac64;
+    float* del32;
+    RunDesc* d_self;       // this run's descriptor in device memory
+    unsigned* ref_bkt;
+    unsigned n_ref_bkt;
     void* ref_keys;
     double *ref_h, *ref_v;
     unsigned* ref_off;
@@ -353,7 +370,19 @@ static int ham_column_dev(const fq_ham* h, int amp, fq_key key, double* diag, fq
     CK(cudaMalloc(&d_m, sizeof(unsigned)));
     unsigned char kbuf[16];
     memcpy(kbuf, &key, 16);
-    ks->column(h->mp, kbuf, d_dest, d_val, ccap, d_diag, d_m, s);
+    ModelParams mp = h->mp;
+    mp.kmax = (mp.N + 1) * (mp.N + 2);
+    double *d_sq = nullptr, *d_hop = nullptr;
+    float* d_hop32 = nullptr;
+    CK(cudaMalloc((void**)&d_sq, sizeof(double) * (mp.kmax + 1)));
+    CK(cudaMalloc((void**)&d_hop, sizeof(double) * (mp.kmax + 1)));
+    CK(cudaMalloc((void**)&d_hop32, sizeof(float) * (mp.kmax + 1)));
+    k_tables<<<(unsigned)((mp.kmax + 256) / 256), 256, 0, s>>>(mp.t, mp.kmax, d_sq, d_hop, d_hop32,
+                                                               0, nullptr, nullptr);
+    mp.sqrt_tab = d_sq;
+    mp.hop_tab = d_hop;
+    mp.hop32_tab = d_hop32;
+    ks->column(mp, kbuf, d_dest, d_val, ccap, d_diag, d_m, s);
     cudaError_t e = cudaStreamSynchronize(s);
     unsigned m = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&m, d_m, sizeof m, cudaMemcpyDeviceToHost);
@@ -370,6 +399,7 @@ static int ham_column_dev(const fq_ham* h, int amp, fq_key key, double* diag, fq
         }
     }
     cudaFree(d_key); cudaFree(d_dest); cudaFree(d_val); cudaFree(d_diag); cudaFree(d_m);
+    cudaFree(d_sq); cudaFree(d_hop); cudaFree(d_hop32);
     if (m_out) *m_out = m;
     return cuda_err(e);
 }
@@ -390,12 +420,40 @@ static size_t max_offdiag(const ModelParams& mp) {
     return (nocc * (nocc + 1) / 2) * (size_t)(mp.M / 2 + 1);
 }
 
+// the run's model with its device tables: every kernel that evaluates
+// matrix elements of the run gets this copy
+static ModelParams run_mp(const fq_run* r) {
+    ModelParams mp = r->ham.mp;
+    mp.kmax = r->tab.kmax;
+    mp.sqrt_tab = r->tab.sq;
+    mp.hop_tab = r->tab.hop;
+    mp.hop32_tab = r->tab.hop32;
+    return mp;
+}
+
 static void fill_desc(const fq_run* r, RunDesc& d, unsigned seg_base) {
     memset(&d, 0, sizeof d);
-    d.mp = r->ham.mp;
+    d.mp = run_mp(r);
+    d.amp = r->amp;
     d.mode_det = r->det;
     d.theta = r->prm.threshold;
     d.t_rel = r->prm.t_rel;
+    d.trel_one = r->prm.t_rel == 1.0;
+    {
+        int e = 0;
+        const double fr = r->det || r->amp == FQ_AMP_INT ? 0.0 : std::frexp(r->prm.threshold, &e);
+        d.theta_pow2 = fr == 0.5;
+        d.theta_exp = e - 1;  // threshold = 2^(e-1) when fr == 1/2
+        d.norm_q = r->amp == FQ_AMP_INT || r->det ? 0 : std::ilogb(r->prm.threshold) - 52;
+    }
+    d.mmax = r->tab.mmax;
+    d.ratio64 = r->tab.r64;
+    d.ratio32 = r->tab.r32;
+    d.smax = r->smax;
+    d.fac64 = r->fac64;
+    d.del32 = r->del32;
+    d.ref_bkt = r->ref_bkt;
+    d.n_ref_bkt = r->n_ref_bkt;
     d.key_x = (unsigned)r->prm.seed;
     d.key_y = (unsigned)(r->prm.seed >> 32) ^ (unsigned)(r->prm.run_id * 0x9E3779B9u);
     d.log2B = r->log2B;
@@ -417,10 +475,16 @@ static void fill_desc(const fq_run* r, RunDesc& d, unsigned seg_base) {
     d.ref_h = r->ref_h;
     d.ref_v = r->ref_v;
     d.ref_off = r->ref_off;
-    d.part_norm = r->part_norm;
     d.part_h = r->part_h;
     d.part_v = r->part_v;
-    d.part_len = r->part_len;
+}
+
+static cudaError_t sync_self(fq_run* r) {
+    RunDesc hd;
+    fill_desc(r, hd, 0);
+    cudaError_t e = cudaMemcpyAsync(r->d_self, &hd, sizeof hd, cudaMemcpyHostToDevice, r->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+    return e;
 }
 
 static LaunchCfg default_cfg(const KernelSet* ks, unsigned slots, unsigned G) {
@@ -517,11 +581,25 @@ extern "C" int fq_run_create(fq_run** out, const fq_ham* h, const fq_params* p, 
     r->skeys = A(kb * (size_t)B * r->Cs);
     r->samps = A(sb * (size_t)B * r->Cs);
     r->sfill = (unsigned*)A(sizeof(unsigned) * B);
-    r->part_norm = (double*)A(sizeof(double) * B);
     r->part_h = (double*)A(sizeof(double) * B);
     r->part_v = (double*)A(sizeof(double) * B);
-    r->part_len = (unsigned long long*)A(sizeof(unsigned long long) * B);
     r->ref_off = (unsigned*)A(sizeof(unsigned) * (B + 1));
+    r->ref_bkt = (unsigned*)A(sizeof(unsigned) * 64 * 1024);
+    r->n_ref_bkt = 0;
+    // matrix-element tables; diagonal factors (real space)
+    const ModelParams& mp0 = h->mp;
+    r->tab.kmax = (mp0.N + 1) * (mp0.N + 2);
+    r->tab.mmax = mp0.kind == FQ_BH_MOM_1D ? 0 : (int)max_offdiag(mp0);
+    r->tab.sq = (double*)A(sizeof(double) * (r->tab.kmax + 1));
+    r->tab.hop = (double*)A(sizeof(double) * (r->tab.kmax + 1));
+    r->tab.hop32 = (float*)A(sizeof(float) * (r->tab.kmax + 1));
+    const size_t nrat = mp0.kind == FQ_BH_MOM_1D ? 0 : (size_t)(r->tab.mmax + 1) * (r->tab.mmax + 1);
+    r->tab.r64 = nrat ? (double*)A(sizeof(double) * nrat) : nullptr;
+    r->tab.r32 = nrat ? (float*)A(sizeof(float) * nrat) : nullptr;
+    r->smax = mp0.kind == FQ_BH_MOM_1D ? -1 : mp0.N * (mp0.N - 1);
+    r->fac64 = r->smax >= 0 ? (double*)A(sizeof(double) * (r->smax + 1)) : nullptr;
+    r->del32 = r->smax >= 0 ? (float*)A(sizeof(float) * (r->smax + 1)) : nullptr;
+    r->d_self = (RunDesc*)A(sizeof(RunDesc));
     r->ref_cap = 0;
     r->ref_keys = nullptr;
     r->ref_h = r->ref_v = nullptr;
@@ -544,6 +622,18 @@ extern "C" int fq_run_create(fq_run** out, const fq_ham* h, const fq_params* p, 
         e = cudaMemsetAsync(r->vcount[i], 0, sizeof(unsigned) * B, r->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->sfill, 0, sizeof(unsigned) * B, r->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->ref_off, 0, sizeof(unsigned) * (B + 1), r->stream);
+    if (e == cudaSuccess) {
+        const long long nt = std::max<long long>(r->tab.kmax + 1, (long long)nrat);
+        k_tables<<<(unsigned)((nt + 255) / 256), 256, 0, r->stream>>>(
+            h->mp.t, r->tab.kmax, r->tab.sq, r->tab.hop, r->tab.hop32, r->tab.mmax, r->tab.r64,
+            r->tab.r32);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        RunDesc hd;
+        fill_desc(r, hd, 0);
+        e = cudaMemcpyAsync(r->d_self, &hd, sizeof hd, cudaMemcpyHostToDevice, r->stream);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
     if (e != cudaSuccess) {
         dev_free_all(r);
@@ -633,19 +723,21 @@ extern "C" int fq_run_seed(fq_run* r, const fq_key* keys, const double* amps, si
     s0.hist_head = 0;
     s0.last_hproj = s0.last_vproj = 0.0;
     s0.last_exact = s0.last_inexact = s0.last_spawns = 0;
+    s0.norm_lo = s0.norm_hi = 0;
+    s0.norm_fp = 0.0;
+    s0.len_acc = 0;
     cudaError_t e = cudaMemcpyAsync(r->st, &s0, sizeof s0, cudaMemcpyHostToDevice, r->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->vcount[0], 0, sizeof(unsigned) * r->B, r->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->vcount[1], 0, sizeof(unsigned) * r->B, r->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->sfill, 0, sizeof(unsigned) * r->B, r->stream);
     if (e == cudaSuccess && m) e = cudaMemcpyAsync(d_k, kbuf.data(), kb * m, cudaMemcpyHostToDevice, r->stream);
     if (e == cudaSuccess && m) e = cudaMemcpyAsync(d_a, sa.data(), sizeof(double) * m, cudaMemcpyHostToDevice, r->stream);
-    RunDesc hd;
-    fill_desc(r, hd, 0);
-    RunDesc* d_desc = nullptr;
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_desc, sizeof(RunDesc));
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_desc, &hd, sizeof hd, cudaMemcpyHostToDevice, r->stream);
     if (e == cudaSuccess) {
-        r->ks->seed(d_desc, d_k, d_a, m, r->stream);
+        r->ks->seed(r->d_self, d_k, d_a, m, r->stream);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && r->smax >= 0) {
+        launch_factors(r->d_self, 1, r->stream);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
@@ -653,7 +745,6 @@ extern "C" int fq_run_seed(fq_run* r, const fq_key* keys, const double* amps, si
     if (e == cudaSuccess) e = cudaMemcpy(&err, &r->st->err, sizeof err, cudaMemcpyDeviceToHost);
     cudaFree(d_k);
     cudaFree(d_a);
-    cudaFree(d_desc);
     if (e != cudaSuccess) return cuda_err(e);
     if (err) {
         unsigned z = 0;
@@ -679,6 +770,9 @@ extern "C" int fq_run_set_reference(fq_run* r, const fq_key* keys, const double*
     const unsigned B = r->B;
     if (n == 0) {
         CK(cudaMemset(r->ref_off, 0, sizeof(unsigned) * (B + 1)));
+        r->n_ref_bkt = 0;
+        r->gen++;
+        CK(sync_self(r));
         return FQ_OK;
     }
     std::vector<unsigned char> kbuf;
@@ -691,7 +785,8 @@ extern "C" int fq_run_set_reference(fq_run* r, const fq_key* keys, const double*
     CK(cudaMalloc((void**)&d_cnt, sizeof(unsigned) * n));
     CK(cudaMemcpy(d_refs, kbuf.data(), kb * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_y, y, sizeof(double) * n, cudaMemcpyHostToDevice));
-    r->ks->ref_count(r->ham.mp, d_refs, (int)n, d_cnt, 0);
+    const ModelParams mp = run_mp(r);
+    r->ks->ref_count(mp, d_refs, (int)n, d_cnt, 0);
     std::vector<unsigned> cnt(n), off(n + 1, 0);
     CK(cudaMemcpy(cnt.data(), d_cnt, sizeof(unsigned) * n, cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < n; ++i) off[i + 1] = off[i] + cnt[i];
@@ -702,7 +797,7 @@ extern "C" int fq_run_set_reference(fq_run* r, const fq_key* keys, const double*
     CK(cudaMalloc((void**)&d_tv, sizeof(double) * T));
     CK(cudaMalloc((void**)&d_tseg, sizeof(unsigned) * T));
     CK(cudaMemcpy(d_off, off.data(), sizeof(unsigned) * (n + 1), cudaMemcpyHostToDevice));
-    r->ks->ref_terms(r->ham.mp, d_refs, d_y, (int)n, d_off, d_tk, d_th, d_tv, d_tseg, r->log2B, 0);
+    r->ks->ref_terms(mp, d_refs, d_y, (int)n, d_off, d_tk, d_th, d_tv, d_tseg, r->log2B, 0);
     CK(cudaDeviceSynchronize());
     std::vector<unsigned char> tk(kb * T);
     std::vector<double> th(T), tv(T);
@@ -740,6 +835,14 @@ extern "C" int fq_run_set_reference(fq_run* r, const fq_key* keys, const double*
     CK(cudaMemcpy(r->ref_h, sh.data(), sizeof(double) * T, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(r->ref_v, sv.data(), sizeof(double) * T, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(r->ref_off, soff.data(), sizeof(unsigned) * (B + 1), cudaMemcpyHostToDevice));
+    std::vector<unsigned> bk;
+    for (unsigned b = 0; b < B; ++b)
+        if (soff[b + 1] > soff[b]) bk.push_back(b);
+    if (bk.size() > 64 * 1024) return FQ_ERR_INVALID;
+    CK(cudaMemcpy(r->ref_bkt, bk.data(), sizeof(unsigned) * bk.size(), cudaMemcpyHostToDevice));
+    r->n_ref_bkt = (unsigned)bk.size();
+    r->gen++;
+    CK(sync_self(r));
     return FQ_OK;
 }
 
@@ -766,6 +869,10 @@ static int set_state_field(fq_run* r, size_t offset, double v) {
     CK(cudaMemcpyAsync((char*)r->st + offset, r->pinned, sizeof(double), cudaMemcpyHostToDevice,
                        r->stream));
     CK(cudaEventRecord(r->staged, r->stream));
+    if (r->smax >= 0 && (offset == offsetof(RunState, shift) || offset == offsetof(RunState, dt))) {
+        launch_factors(r->d_self, 1, r->stream);
+        CK(cudaGetLastError());
+    }
     return FQ_OK;
 }
 
@@ -914,6 +1021,9 @@ static int run_check(fq_run* r) {
     CK(cudaMemcpy(&s, r->st, sizeof s, cudaMemcpyDeviceToHost));
     s.err = 0;
     s.n_exact = s.n_inexact = s.n_spawns = 0;
+    s.norm_lo = s.norm_hi = 0;
+    s.norm_fp = 0.0;
+    s.len_acc = 0;
     CK(cudaMemcpy(r->st, &s, sizeof s, cudaMemcpyHostToDevice));
     CK(cudaMemset(r->sfill, 0, sizeof(unsigned) * r->B));
     if (err & FQ_DERR_EMPTY) return FQ_ERR_EMPTY;

@@ -205,18 +205,32 @@ template <int KIND> struct RealModel {
         c.n_occ = KeyOps<K>::popc(run_starts(k));
         return (unsigned)(Z * c.n_occ);
     }
-    // k-th off-diagonal entry of the column at `key`
-    template <class K>
+    // k-th off-diagonal entry of the column at `key`; val in FP64, or the
+    // FP32 rounding of the same FP64 value
+    template <class K, class V>
     __device__ __forceinline__ static K offdiag(const ModelParams& p, K key, const Col& c, unsigned kk,
-                                                double& val) {
+                                                V& val) {
         const int d = (int)(kk / (unsigned)c.n_occ), r = (int)(kk % (unsigned)c.n_occ);
         const int P = KeyOps<K>::nth(run_starts(key), r);
         const int s = P - KeyOps<K>::popc(key & KeyOps<K>::low(P));
         const int ns = run_from(key, P);
         const int s2 = neighbour(p, s, d);
         const int nt = mode_occ(key, s2);
-        val = -(p.t * sqrt((double)(ns * (nt + 1))));
+        // -(t sqrt(n_s (n_s' + 1))) from the table
+        if constexpr (sizeof(V) == 4) val = __ldg(p.hop32_tab + ns * (nt + 1));
+        else val = __ldg(p.hop_tab + ns * (nt + 1));
         return add_boson(del_bit(key, P), s2);
+    }
+    // sum over modes of n (n - 1): H_ii = (u/2) times this
+    template <class K> __device__ __forceinline__ static int diag_index(K k) {
+        K st = run_starts(k);
+        int s = 0;
+        while (st) {
+            const int n = run_from(k, KeyOps<K>::ctz(st));
+            s += n * (n - 1);
+            st &= st - 1;
+        }
+        return s;
     }
 };
 
@@ -286,9 +300,9 @@ struct MomModel {
         j = i + 1 + (int)t;
     }
 
-    template <class K>
+    template <class K, class V>
     __device__ __forceinline__ static K offdiag(const ModelParams& pm, K key, const Col& c, unsigned kk,
-                                                double& val) {
+                                                V& val) {
         const int M = pm.M;
         const uint64_t E = c.occm & 0x5555555555555555ull, O = c.occm & 0xAAAAAAAAAAAAAAAAull;
         int p, q;
@@ -327,10 +341,137 @@ struct MomModel {
         const long long nr = mode_occ(k1, r), ns = mode_occ(k1, s);
         const long long B = (nr + 1) * (ns + 1 + (r == s ? 1 : 0));
         const int F = (p != q ? 2 : 1) * (r != s ? 2 : 1);
-        val = (pm.g * (double)F) * sqrt((double)(A * B));
+        val = (V)(((pm.g * (double)F) * __ldg(pm.sqrt_tab + A)) * __ldg(pm.sqrt_tab + B));
         return add_boson(add_boson(k1, r), s);
     }
 };
+
+// ---------------------------------------------------------------------------
+// exact bit-level arithmetic: GB300 issues FP64 at a small fraction of its
+// FP32/INT rate, so every operation whose result is exact is done on the
+// integer bits instead (same results as the FP64 expressions they replace)
+
+__device__ __forceinline__ unsigned long long dbits(double x) {
+    return (unsigned long long)__double_as_longlong(x);
+}
+__device__ __forceinline__ double bdouble(unsigned long long b) {
+    return __longlong_as_double((long long)b);
+}
+constexpr unsigned long long ABS64 = 0x7FFFFFFFFFFFFFFFull;
+constexpr unsigned ABS32 = 0x7FFFFFFFu;
+
+// floor(|x|) and ceil(|x|) of a finite double, saturated at 2^32 - 1
+__device__ __forceinline__ void floor_ceil_abs(double x, unsigned& fl, unsigned& ce) {
+    const unsigned long long b = dbits(x) & ABS64;
+    const int E = (int)(b >> 52);
+    if (b == 0) { fl = ce = 0; return; }
+    if (E < 1023) { fl = 0; ce = 1; return; }
+    const int e = E - 1023;
+    if (e >= 32) { fl = ce = 0xFFFFFFFFu; return; }
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+    const unsigned long long f = m >> (52 - e);
+    fl = (unsigned)f;
+    ce = (unsigned)f + ((m & ((1ull << (52 - e)) - 1)) ? 1u : 0u);
+}
+__device__ __forceinline__ void floor_ceil_abs(float x, unsigned& fl, unsigned& ce) {
+    const unsigned b = __float_as_uint(x) & ABS32;
+    const int E = (int)(b >> 23);
+    if (b == 0) { fl = ce = 0; return; }
+    if (E < 127) { fl = 0; ce = 1; return; }
+    const int e = E - 127;
+    if (e >= 32) { fl = ce = 0xFFFFFFFFu; return; }
+    const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+    if (e >= 23) { fl = ce = (unsigned)(m << (e - 23)); return; }
+    const unsigned long long f = m >> (23 - e);
+    fl = (unsigned)f;
+    ce = (unsigned)f + ((m & ((1ull << (23 - e)) - 1)) ? 1u : 0u);
+}
+
+// 53 random bits of a draw: the integer u53 with uniform53 = u53 * 2^-53
+__device__ __forceinline__ unsigned long long u53_of(uint4 w) {
+    return ((unsigned long long)(w.x >> 5) << 26) | (unsigned long long)(w.y >> 6);
+}
+
+// u53 * 2^-53 < a * 2^-e for a = m53 * 2^(E - 1075) (biased exponent E,
+// E >= 1 normal), decided exactly in integers: with k = 1022 + e - E the
+// test is u53 * 2^k < m53 (k >= 0 whenever a < 2^e)
+__device__ __forceinline__ bool below_scaled(unsigned long long u53, unsigned long long abits,
+                                             int e) {
+    const int E = (int)(abits >> 52);
+    unsigned long long m;
+    int k;
+    if (E == 0) {  // subnormal: a = m 2^(1 - 1075)
+        m = abits & 0xFFFFFFFFFFFFFull;
+        k = 1021 + e;
+    } else {
+        m = (abits & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+        k = 1022 + e - E;
+    }
+    if (k < 0) return true;  // a >= 2^e (not reached by callers)
+    if (k >= 64) return u53 == 0 && m != 0;
+    if (k > 0 && (u53 >> (64 - k))) return false;
+    return (u53 << k) < m;
+}
+
+// bits of (double)|x| for a float x
+__device__ __forceinline__ unsigned long long abs_dbits(float x) {
+    const unsigned b = __float_as_uint(x) & ABS32;
+    if (b == 0) return 0ull;
+    if ((b >> 23) == 0) return dbits(fabs((double)x));  // subnormal float
+    return ((unsigned long long)((b >> 23) - 127 + 1023) << 52) |
+           ((unsigned long long)(b & 0x7FFFFFu) << 29);
+}
+__device__ __forceinline__ unsigned long long abs_dbits(double x) { return dbits(x) & ABS64; }
+
+// (hi:lo) 2^q rounded to the nearest double, ties to even
+__device__ __forceinline__ double fixed_to_double(unsigned long long lo, unsigned long long hi,
+                                                  int q) {
+    if (!hi) return scalbn(__ull2double_rn(lo), q);
+    const int lz = __clzll((long long)hi);
+    const int sh = 64 - lz;
+    unsigned long long top = sh == 64 ? hi : ((hi << lz) | (lo >> sh));
+    const unsigned long long rest = sh == 64 ? lo : (lo & ((1ull << sh) - 1ull));
+    if (rest) top |= 1ull;
+    return scalbn(__ull2double_rn(top), q + sh);
+}
+
+// |x| in units of 2^q as a 128-bit integer (|x| >= 2^(q + 52) so it is
+// integral); sets `bad` when it would not fit in 2^116
+__device__ __forceinline__ void fixed_of(double x, int q, unsigned long long& lo,
+                                         unsigned long long& hi, bool& bad) {
+    const unsigned long long b = dbits(x) & ABS64;
+    lo = hi = 0;
+    if (!b) return;
+    const int E = (int)(b >> 52);
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+    const int sh = E - 1075 - q;  // |x| = m 2^(E - 1075)
+    if (E == 0 || sh < 0 || sh > 63) { bad = true; return; }
+    lo = m << sh;
+    hi = sh ? (m >> (64 - sh)) : 0ull;
+}
+__device__ __forceinline__ void fixed_of(float x, int q, unsigned long long& lo,
+                                         unsigned long long& hi, bool& bad) {
+    const unsigned b = __float_as_uint(x) & ABS32;
+    lo = hi = 0;
+    if (!b) return;
+    const int E = (int)(b >> 23);
+    const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+    const int sh = E - 150 - q;  // |x| = m 2^(E - 150)
+    if (E == 0 || sh < 0 || sh > 63 + 40) { bad = true; return; }
+    if (sh < 64) {
+        lo = m << sh;
+        hi = sh ? (m >> (64 - sh)) : 0ull;
+    } else {
+        lo = 0;
+        hi = m << (sh - 64);
+    }
+}
+__device__ __forceinline__ void add128(unsigned long long& lo, unsigned long long& hi,
+                                       unsigned long long blo, unsigned long long bhi) {
+    const unsigned long long l = lo + blo;
+    hi += bhi + (l < lo ? 1ull : 0ull);
+    lo = l;
+}
 
 template <> struct Model<FQ_KIND_REAL_1D> : RealModel<FQ_KIND_REAL_1D> {};
 template <> struct Model<FQ_KIND_REAL_2D> : RealModel<FQ_KIND_REAL_2D> {};

@@ -3,25 +3,31 @@
 //
 //   k_spawn  For every occupied entry c_i of c^(n): decide an exact or a
 //            stochastic column (|c_i| t_rel >= m_i, Sec. 7.1), then write the
-//            column's spawns -dt H_ji c_i (exact) or n_i = ceil|c_i| uniform
-//            picks scaled by m_i/n_i (Eq. column-compression) into the bucket
-//            that owns each destination address.
+//            column's spawns H_ji coef_i, coef_i = -dt c_i (exact) or
+//            -dt (m_i / n_i) c_i for n_i = ceil|c_i| uniform picks (Eq.
+//            column-compression), into the bucket owning each destination.
 //   k_merge  For every bucket: put c^(n)'s segment, with the diagonal factor
 //            1 + dt (S - H_ii) applied, and every spawn to the bucket into an
 //            on-chip open-addressing table, which sums contributions per
 //            address (annihilation); apply vector compression Pi (Eq.
 //            vec-compression); compact the survivors into c^(n+1)'s
-//            segment; reduce ||c||_1, len and the projected-energy terms.
-//   k_shift  One block per run: reduce the per-segment partial sums in a
-//            fixed order, apply Eq. shift-update, append a history row and
-//            flip the vector buffers.
+//            segment; accumulate ||c||_1 (exactly), len and the
+//            projected-energy terms.
+//   k_shift  One block per run: Eq. shift-update, a history row, the buffer
+//            flip, and the diagonal-factor table of the next step.
 //
 // Layout: the vector of a run is hash-segmented (the paper's PDVec segments,
-// Sec. 6.4, with thousands of small segments sized for one SM's shared
+// Sec. 6.4, as thousands of small segments sized for one SM's shared
 // memory): segment b = top log2(B) bits of fmix64(h(address)), capacity Cv
 // entries each, structure-of-arrays keys/amplitudes.  Spawn buckets use the
 // same segment map with capacity Cs.  All sizes and pointers are read from
 // device memory, so one captured CUDA graph replays any number of steps.
+//
+// GB300 executes FP64 at a small fraction of its FP32/integer rate, so the
+// kernels keep FP64 work to about one multiply per spawn and per entry (FP64
+// amplitudes) or none (FP32 amplitudes); decisions whose result is exact are
+// taken on integer bits (fq_device.cuh), with results identical to the FP64
+// expressions they stand for.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -32,9 +38,14 @@
 namespace fq {
 
 template <int AMP> struct AmpT;
-template <> struct AmpT<FQ_AMP_INT> { typedef long long A; typedef int S; typedef long long ACC; };
-template <> struct AmpT<FQ_AMP_F64> { typedef double A; typedef double S; typedef double ACC; };
-template <> struct AmpT<FQ_AMP_F32> { typedef float A; typedef float S; typedef double ACC; };
+template <> struct AmpT<FQ_AMP_INT> {
+    typedef long long A;    // stored amplitude
+    typedef int S;          // spawn value
+    typedef long long ACC;  // on-chip sum
+    typedef double C;       // per-source coefficient
+};
+template <> struct AmpT<FQ_AMP_F64> { typedef double A, S, ACC, C; };
+template <> struct AmpT<FQ_AMP_F32> { typedef float A, S, ACC, C; };
 
 // ---------------------------------------------------------------------------
 // block-wide helpers (deterministic for a fixed block size)
@@ -85,6 +96,42 @@ __device__ __forceinline__ T block_sum(T v, T* s_red) {
     return r;  // valid in thread 0
 }
 
+// exact 128-bit sum over the block; valid in thread 0
+template <int BLOCK>
+__device__ __forceinline__ void block_sum128(unsigned long long& lo, unsigned long long& hi,
+                                             unsigned long long* s_red) {
+    constexpr int NW = BLOCK / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long l = __shfl_down_sync(0xFFFFFFFFu, lo, o);
+        const unsigned long long h = __shfl_down_sync(0xFFFFFFFFu, hi, o);
+        add128(lo, hi, l, h);
+    }
+    if (lane == 0) {
+        s_red[2 * warp] = lo;
+        s_red[2 * warp + 1] = hi;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        lo = lane < NW ? s_red[2 * lane] : 0ull;
+        hi = lane < NW ? s_red[2 * lane + 1] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long l = __shfl_down_sync(0xFFFFFFFFu, lo, o);
+            const unsigned long long h = __shfl_down_sync(0xFFFFFFFFu, hi, o);
+            add128(lo, hi, l, h);
+        }
+    }
+    __syncthreads();
+}
+
+// contiguous range of segments for this block
+__device__ __forceinline__ void block_range(unsigned G, unsigned& g0, unsigned& g1) {
+    g0 = (unsigned)(((unsigned long long)G * blockIdx.x) / gridDim.x);
+    g1 = (unsigned)(((unsigned long long)G * (blockIdx.x + 1)) / gridDim.x);
+}
+
 // ---------------------------------------------------------------------------
 // K1: spawning
 
@@ -93,32 +140,57 @@ __global__ void __launch_bounds__(BLOCK)
 k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, unsigned G) {
     typedef typename AmpT<AMP>::A A;
     typedef typename AmpT<AMP>::S S;
+    typedef typename AmpT<AMP>::C CO;
     typedef Model<KIND> MD;
     typedef typename MD::Col Col;
     constexpr int CH = BLOCK * IPT;
     __shared__ K s_key[CH];
-    __shared__ double s_amp[CH];
+    __shared__ CO s_coef[CH];
     __shared__ unsigned s_off[CH + 1];
     __shared__ unsigned s_m[CH];
     __shared__ unsigned s_warp[BLOCK / 32];
     __shared__ unsigned long long s_red[BLOCK / 32];
-    __shared__ unsigned s_ctl[4];
+    __shared__ unsigned s_ctl[2];
     const int tid = threadIdx.x;
+    unsigned g0, g1;
+    block_range(G, g0, g1);
 
-    for (unsigned g = blockIdx.x; g < G; g += gridDim.x) {
-        const RunDesc* R = runs + seg_run[g];
-        const unsigned seg = g - R->seg_base;
-        RunState* st = R->st;
-        if (tid == 0) {
-            const int cur = st->cur;
-            s_ctl[0] = *(volatile unsigned*)&st->err;
-            s_ctl[1] = (unsigned)cur;
-            s_ctl[2] = R->vcount[cur][seg];
+    const RunDesc* R = nullptr;
+    int cur_r = -1;
+    unsigned err = 0, cur = 0;
+    unsigned long long n_ex = 0, n_inex = 0, n_sp = 0;
+
+    for (unsigned g = g0; g < g1; ++g) {
+        const int r = (int)seg_run[g];
+        if (r != cur_r) {  // uniform: every thread reads the same r
+            if (R) {
+                const unsigned long long e = block_sum<BLOCK>(n_ex, s_red);
+                const unsigned long long ie = block_sum<BLOCK>(n_inex, s_red);
+                const unsigned long long sp = block_sum<BLOCK>(n_sp, s_red);
+                if (tid == 0) {
+                    if (e) atomicAdd(&R->st->n_exact, e);
+                    if (ie) atomicAdd(&R->st->n_inexact, ie);
+                    if (sp) atomicAdd(&R->st->n_spawns, sp);
+                }
+                n_ex = n_inex = n_sp = 0;
+            }
+            R = runs + r;
+            cur_r = r;
+            // one thread reads, all use the same values: another block may
+            // set an error bit meanwhile
+            if (tid == 0) {
+                s_ctl[0] = *(volatile unsigned*)&R->st->err;
+                s_ctl[1] = (unsigned)R->st->cur;
+            }
+            __syncthreads();
+            err = s_ctl[0];
+            cur = s_ctl[1];
+            __syncthreads();
         }
-        __syncthreads();
-        const unsigned err = s_ctl[0], cur = s_ctl[1], n = s_ctl[2];
-        __syncthreads();
-        if (err || n == 0) continue;
+        if (err) continue;
+        const unsigned seg = g - R->seg_base;
+        const unsigned n = R->vcount[cur][seg];
+        if (n == 0) continue;
 
         const ModelParams& mp = R->mp;
         const K* __restrict__ vk = (const K*)R->vkeys[cur] + (size_t)seg * R->Cv;
@@ -128,42 +200,68 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
         unsigned* __restrict__ sfill = R->sfill;
         const unsigned Cs = R->Cs;
         const int log2B = R->log2B;
-        const double dt = st->dt, t_rel = R->t_rel;
-        const int det = R->mode_det;
-        const unsigned stepno = (unsigned)(st->step + 1);
+        const double dt = R->st->dt;
+        const int det = R->mode_det, trel_one = R->trel_one;
+        const double t_rel = R->t_rel;
+        const int mmax = R->mmax;
+        const unsigned stepno = (unsigned)(R->st->step + 1);
         const uint2 rkey = make_uint2(R->key_x, R->key_y);
-        unsigned long long n_ex = 0, n_inex = 0, n_sp = 0;
 
         for (unsigned c0 = 0; c0 < n; c0 += CH) {
             const unsigned cn = min((unsigned)CH, n - c0);
+            // stage keys and amplitudes (coalesced); amplitudes go through
+            // s_coef, overwritten by the coefficients below
 #pragma unroll
             for (int j = 0; j < IPT; ++j) {
                 const unsigned i = j * BLOCK + tid;
                 if (i < cn) {
                     s_key[i] = vk[c0 + i];
-                    s_amp[i] = (double)va[c0 + i];
+                    s_coef[i] = (CO)va[c0 + i];
                 }
             }
             __syncthreads();
             unsigned cnt[IPT], tsum = 0;
+            CO coef[IPT];
 #pragma unroll
             for (int j = 0; j < IPT; ++j) {
                 const unsigned i = tid * IPT + j;
                 unsigned c_i = 0;
+                coef[j] = (CO)0;
                 if (i < cn) {
                     const K key = s_key[i];
-                    const double c = s_amp[i];
+                    const CO c = s_coef[i];
                     Col col;
                     const unsigned m = MD::num_offdiag(mp, key, col);
+                    unsigned fl, ce;
+                    floor_ceil_abs(c, fl, ce);
                     if (AMP == FQ_AMP_INT) {
-                        // integer walkers: |c| attempts, never an exact column
-                        c_i = m ? (unsigned)fabs(c) : 0u;
+                        // integer walkers: |c| attempts, never an exact column;
+                        // the coefficient is dt m (spawn probability per |H_ji|)
+                        c_i = m ? fl : 0u;
                         ++n_inex;
-                        s_m[i] = m;
+                        coef[j] = (CO)(dt * (double)m);
+                        s_m[i] = m | (c < (CO)0 ? 0x40000000u : 0u);
                     } else {
-                        const bool ex = det || fabs(c) * t_rel >= (double)m;
-                        c_i = ex ? m : (unsigned)ceil(fabs(c));
-                        if (ex) ++n_ex; else ++n_inex;
+                        bool ex;
+                        if (det) ex = true;
+                        else if (trel_one) ex = fl >= m;  // |c| >= m for an integer m
+                        else ex = fabs((double)c) * t_rel >= (double)m;
+                        c_i = ex ? m : ce;
+                        if (ex) {
+                            ++n_ex;
+                            coef[j] = (-(CO)dt) * c;
+                        } else {
+                            ++n_inex;
+                            CO ratio;
+                            if (KIND != FQ_KIND_MOM_1D && (int)m <= mmax && (int)ce <= mmax) {
+                                const size_t ri = (size_t)m * (size_t)(mmax + 1) + ce;
+                                if constexpr (AMP == FQ_AMP_F32) ratio = __ldg(R->ratio32 + ri);
+                                else ratio = __ldg(R->ratio64 + ri);
+                            } else {
+                                ratio = (CO)m / (CO)ce;
+                            }
+                            coef[j] = ((-(CO)dt) * ratio) * c;
+                        }
                         s_m[i] = m | (ex ? 0x80000000u : 0u);
                     }
                 }
@@ -175,80 +273,99 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
 #pragma unroll
             for (int j = 0; j < IPT; ++j) {
                 s_off[tid * IPT + j] = off;
+                s_coef[tid * IPT + j] = coef[j];
                 off += cnt[j];
             }
             if (tid == 0) s_off[CH] = total;
             __syncthreads();
 
-            for (unsigned q = tid; q < total; q += BLOCK) {
-                int lo = 0, hi = CH - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (s_off[mid] <= q) lo = mid; else hi = mid - 1;
+            // each thread takes a contiguous run of spawn indices
+            const unsigned q0 = (unsigned)(((unsigned long long)total * tid) / BLOCK);
+            const unsigned q1 = (unsigned)(((unsigned long long)total * (tid + 1)) / BLOCK);
+            if (q0 < q1) {
+                int i;
+                {
+                    int lo = 0, hi = CH - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_off[mid] <= q0) lo = mid; else hi = mid - 1;
+                    }
+                    i = lo;
                 }
-                const unsigned a = q - s_off[lo];
-                const K key = s_key[lo];
-                const double c = s_amp[lo];
-                const unsigned mm = s_m[lo];
-                const unsigned m = mm & 0x7FFFFFFFu;
-                const bool ex = (AMP != FQ_AMP_INT) && (mm >> 31);
+                K key = s_key[i];
+                CO cf = s_coef[i];
+                unsigned mm = s_m[i];
+                unsigned end_i = s_off[i + 1];
                 Col col;
                 MD::num_offdiag(mp, key, col);
-                uint4 w = make_uint4(0, 0, 0, 0);
-                unsigned kk = a;
-                if (!ex) {
-                    w = draw(rkey, stepno, a, KeyOps<K>::rng_h(key));
-                    kk = pick(w, m);
-                }
-                double hv;
-                const K dest = MD::offdiag(mp, key, col, kk, hv);
-                S val;
-                if (AMP == FQ_AMP_INT) {
-                    const double p = (dt * fabs(hv)) * (double)m;
-                    const double fl = floor(p);
-                    const long long nw = (long long)fl + (uniform53(w) < p - fl ? 1 : 0);
-                    if (!nw) continue;
-                    const int sg = (hv > 0.0 ? -1 : 1) * (c > 0.0 ? 1 : -1);
-                    val = (S)(sg * nw);
-                } else if (ex) {
-                    val = (S)((-(dt * hv)) * c);
-                } else {
-                    const double scale = (double)m / ceil(fabs(c));
-                    val = (S)(((-(dt * hv)) * scale) * c);
-                }
-                ++n_sp;
-                const unsigned b = segment_of(fmix64(KeyOps<K>::rng_h(dest)), log2B);
-                const unsigned pos = atomicAdd(&sfill[b], 1u);
-                if (pos < Cs) {
-                    sk[(size_t)b * Cs + pos] = dest;
-                    sv[(size_t)b * Cs + pos] = val;
-                } else {
-                    atomicOr(&st->err, FQ_DERR_SPAWN_CAP);
+                for (unsigned q = q0; q < q1; ++q) {
+                    if (q >= end_i) {
+                        do { ++i; } while (q >= s_off[i + 1]);
+                        key = s_key[i];
+                        cf = s_coef[i];
+                        mm = s_m[i];
+                        end_i = s_off[i + 1];
+                        MD::num_offdiag(mp, key, col);
+                    }
+                    const unsigned a = q - s_off[i];
+                    const unsigned m = mm & 0x3FFFFFFFu;
+                    const bool ex = (AMP != FQ_AMP_INT) && (mm >> 31);
+                    uint4 w = make_uint4(0, 0, 0, 0);
+                    unsigned kk = a;
+                    if (!ex) {
+                        w = draw(rkey, stepno, a, KeyOps<K>::rng_h(key));
+                        kk = pick(w, m);
+                    }
+                    S val;
+                    K dest;
+                    if constexpr (AMP == FQ_AMP_INT) {
+                        double hv;
+                        dest = MD::offdiag(mp, key, col, kk, hv);
+                        const double p = fabs(hv) * cf;
+                        const double fl = floor(p);
+                        const long long nw = (long long)fl + (uniform53(w) < p - fl ? 1 : 0);
+                        if (!nw) continue;
+                        const int sg = (hv > 0.0 ? -1 : 1) * ((mm & 0x40000000u) ? -1 : 1);
+                        val = (S)(sg * nw);
+                    } else {
+                        CO hv;
+                        dest = MD::offdiag(mp, key, col, kk, hv);
+                        val = hv * cf;
+                    }
+                    ++n_sp;
+                    const unsigned b = segment_of(fmix64(KeyOps<K>::rng_h(dest)), log2B);
+                    const unsigned pos = atomicAdd(&sfill[b], 1u);
+                    if (pos < Cs) {
+                        sk[(size_t)b * Cs + pos] = dest;
+                        sv[(size_t)b * Cs + pos] = val;
+                    } else {
+                        atomicOr(&R->st->err, FQ_DERR_SPAWN_CAP);
+                    }
                 }
             }
             __syncthreads();
         }
+    }
+    if (R) {
         const unsigned long long e = block_sum<BLOCK>(n_ex, s_red);
         const unsigned long long ie = block_sum<BLOCK>(n_inex, s_red);
         const unsigned long long sp = block_sum<BLOCK>(n_sp, s_red);
         if (tid == 0) {
-            if (e) atomicAdd(&st->n_exact, e);
-            if (ie) atomicAdd(&st->n_inexact, ie);
-            if (sp) atomicAdd(&st->n_spawns, sp);
+            if (e) atomicAdd(&R->st->n_exact, e);
+            if (ie) atomicAdd(&R->st->n_inexact, ie);
+            if (sp) atomicAdd(&R->st->n_spawns, sp);
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// accumulation into a table slot: FP64 add, or a two's-complement add for
-// integer walkers (exact in any order)
+// on-chip open-addressing table (linear probing, CAS on the key)
+
 __device__ __forceinline__ void acc_add(double* p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void acc_add(float* p, float v) { atomicAdd(p, v); }
 __device__ __forceinline__ void acc_add(long long* p, long long v) {
     atomicAdd((unsigned long long*)p, (unsigned long long)v);
 }
-
-// ---------------------------------------------------------------------------
-// on-chip open-addressing table (linear probing, CAS on the key)
 
 __device__ __forceinline__ uint64_t key_cas(uint64_t* p, uint64_t cmp, uint64_t val) {
     return (uint64_t)atomicCAS((unsigned long long*)p, (unsigned long long)cmp,
@@ -258,20 +375,23 @@ __device__ __forceinline__ u128 key_cas(u128* p, u128 cmp, u128 val) {
     return atomicCAS(p, cmp, val);
 }
 
+// slot of `key`, inserting it if absent (is_new set); -1 when the table is full
 template <class K>
-__device__ __forceinline__ int table_insert(K* tkey, unsigned mask, K key) {
+__device__ __forceinline__ int table_insert(K* tkey, unsigned mask, K key, bool& is_new) {
     const K EMPTY = KeyOps<K>::empty();
     unsigned q = (unsigned)fmix64(KeyOps<K>::rng_h(key)) & mask;
+    is_new = false;
     for (unsigned probe = 0; probe <= mask; ++probe) {
         const K seen = tkey[q];
         if (seen == key) return (int)q;
         if (seen == EMPTY) {
             const K old = key_cas(&tkey[q], EMPTY, key);
-            if (old == EMPTY || old == key) return (int)q;
+            if (old == EMPTY) { is_new = true; return (int)q; }
+            if (old == key) return (int)q;
         }
         q = (q + 1) & mask;
     }
-    return -1;  // table full
+    return -1;
 }
 
 template <class K>
@@ -287,9 +407,70 @@ __device__ __forceinline__ int table_find(const K* tkey, unsigned mask, K key) {
     return -1;
 }
 
+// Pi (Eq. vec-compression) of one merged value: keep |w| >= theta, else
+// sign(w) theta with probability |w| / theta.  `out` is the stored value.
+template <int AMP>
+__device__ __forceinline__ bool compress(typename AmpT<AMP>::ACC w, const RunDesc* R, uint2 rkey,
+                                         unsigned stepno, uint64_t h,
+                                         typename AmpT<AMP>::ACC& out) {
+    typedef typename AmpT<AMP>::ACC ACC;
+    if constexpr (AMP == FQ_AMP_INT) {
+        out = w;
+        return w != 0;
+    } else {
+        const unsigned long long ab = abs_dbits(w);
+        if (R->mode_det) {
+            out = w;
+            return ab != 0;
+        }
+        if (ab == 0) return false;
+        const double theta = R->theta;
+        if (R->theta_pow2) {
+            if (ab >= dbits(theta)) {
+                out = w;
+                return true;
+            }
+            const uint4 r = draw(rkey, stepno, 0xFFFFFFFFu, h);
+            if (!below_scaled(u53_of(r), ab, R->theta_exp)) return false;
+        } else {
+            const double aw = bdouble(ab);
+            if (aw >= theta) {
+                out = w;
+                return true;
+            }
+            const uint4 r = draw(rkey, stepno, 0xFFFFFFFFu, h);
+            if (!(uniform53(r) < aw / theta)) return false;
+        }
+        out = w < (ACC)0 ? (ACC)(-theta) : (ACC)theta;
+        return true;
+    }
+}
+
+// add a block's share of one run's step totals to the run's accumulators
+template <int BLOCK>
+__device__ __forceinline__ void merge_flush(const RunDesc* R, unsigned long long nlo,
+                                            unsigned long long nhi, unsigned long long nlen,
+                                            double nfp, bool full, bool over, bool range_bad,
+                                            unsigned long long* s_red, double* s_redd) {
+    block_sum128<BLOCK>(nlo, nhi, s_red);
+    const unsigned long long ln = block_sum<BLOCK>(nlen, s_red);
+    const double fp = block_sum<BLOCK>(nfp, s_redd);
+    const int f = __syncthreads_or(full), o = __syncthreads_or(over),
+              b = __syncthreads_or(range_bad);
+    if (threadIdx.x == 0) {
+        const unsigned long long old = atomicAdd(&R->st->norm_lo, nlo);
+        atomicAdd(&R->st->norm_hi, nhi + (old + nlo < old ? 1ull : 0ull));
+        atomicAdd(&R->st->len_acc, ln);
+        if (R->mode_det) atomicAdd(&R->st->norm_fp, fp);
+        if (f) atomicOr(&R->st->err, FQ_DERR_TABLE);
+        if (o) atomicOr(&R->st->err, FQ_DERR_VEC_CAP);
+        if (b) atomicOr(&R->st->err, FQ_DERR_RANGE);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // K4: diagonal update + annihilation + vector compression + compaction +
-//     estimator partial sums, one bucket per block iteration
+//     estimator accumulation, one bucket per block iteration
 
 template <class K, int AMP, int KIND, int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
@@ -302,31 +483,56 @@ k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     extern __shared__ __align__(16) unsigned char smem[];
     K* tkey = (K*)smem;
     ACC* tacc = (ACC*)(smem + (size_t)SLOTS * sizeof(K));
-    __shared__ unsigned s_warp[BLOCK / 32];
+    unsigned short* tlist = (unsigned short*)(smem + (size_t)SLOTS * (sizeof(K) + sizeof(ACC)));
+    __shared__ unsigned long long s_red[2 * (BLOCK / 32)];
     __shared__ double s_redd[BLOCK / 32];
-    __shared__ unsigned s_ctl[4];
-    const int tid = threadIdx.x;
+    __shared__ unsigned s_nlist, s_nout;
+    __shared__ unsigned s_ctl[2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned mask = SLOTS - 1;
-    const unsigned spt = SLOTS / BLOCK;
     const K EMPTY = KeyOps<K>::empty();
 
-    for (unsigned g = blockIdx.x; g < G; g += gridDim.x) {
-        const RunDesc* R = runs + seg_run[g];
-        const unsigned seg = g - R->seg_base;
-        RunState* st = R->st;
-        if (tid == 0) {
-            const int cur = st->cur;
-            s_ctl[0] = *(volatile unsigned*)&st->err;
-            s_ctl[1] = (unsigned)cur;
-            s_ctl[2] = R->vcount[cur][seg];
-            s_ctl[3] = R->sfill[seg];
-        }
-        __syncthreads();
-        const unsigned err = s_ctl[0], cur = s_ctl[1], n_old = s_ctl[2], n_sp = s_ctl[3];
-        __syncthreads();
-        if (err) continue;
+    for (unsigned q = tid; q < SLOTS; q += BLOCK) {
+        tkey[q] = EMPTY;
+        tacc[q] = (ACC)0;
+    }
+    unsigned g0, g1;
+    block_range(G, g0, g1);
 
-        const ModelParams& mp = R->mp;
+    const RunDesc* R = nullptr;
+    int cur_r = -1;
+    unsigned err = 0, cur = 0;
+    unsigned long long nlo = 0, nhi = 0, nlen = 0;
+    double nfp = 0.0;
+    bool range_bad = false, full = false, over = false;
+    __syncthreads();
+
+    for (unsigned g = g0; g < g1; ++g) {
+        const int r = (int)seg_run[g];
+        if (r != cur_r) {  // uniform
+            if (R) {
+                merge_flush<BLOCK>(R, nlo, nhi, nlen, nfp, full, over, range_bad, s_red, s_redd);
+                nlo = nhi = nlen = 0;
+                nfp = 0.0;
+                full = over = range_bad = false;
+            }
+            R = runs + r;
+            cur_r = r;
+            // one thread reads, all use the same values: another block may
+            // set an error bit meanwhile
+            if (tid == 0) {
+                s_ctl[0] = *(volatile unsigned*)&R->st->err;
+                s_ctl[1] = (unsigned)R->st->cur;
+            }
+            __syncthreads();
+            err = s_ctl[0];
+            cur = s_ctl[1];
+            __syncthreads();
+        }
+        if (err) continue;
+        const unsigned seg = g - R->seg_base;
+        const unsigned n_old = R->vcount[cur][seg];
+        const unsigned n_sp = R->sfill[seg];
         const unsigned Cv = R->Cv;
         const K* __restrict__ vk = (const K*)R->vkeys[cur] + (size_t)seg * Cv;
         const A* __restrict__ va = (const A*)R->vamps[cur] + (size_t)seg * Cv;
@@ -334,114 +540,165 @@ k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
         A* __restrict__ oa = (A*)R->vamps[cur ^ 1] + (size_t)seg * Cv;
         const K* __restrict__ sk = (const K*)R->skeys + (size_t)seg * R->Cs;
         const S* __restrict__ sv = (const S*)R->samps + (size_t)seg * R->Cs;
-        const double S0 = st->shift, dt = st->dt, theta = R->theta;
-        const int det = R->mode_det;
-        const unsigned stepno = (unsigned)(st->step + 1);
+        const unsigned stepno = (unsigned)(R->st->step + 1);
         const uint2 rkey = make_uint2(R->key_x, R->key_y);
-
-        for (unsigned q = tid; q < SLOTS; q += BLOCK) {
-            tkey[q] = EMPTY;
-            tacc[q] = (ACC)0;
+        const int nq = R->norm_q;
+        const int det = R->mode_det;
+        if (tid == 0) {
+            s_nlist = n_old;
+            s_nout = 0;
         }
-        __syncthreads();
 
         // diagonal term c_i (1 + dt (S - H_ii)); integer walkers round it
         // stochastically
-        bool full = false;
         for (unsigned i = tid; i < n_old; i += BLOCK) {
             const K key = vk[i];
-            const double c = (double)va[i];
-            const double hii = MD::diagonal(mp, key);
-            const double x = c * (1.0 + dt * (S0 - hii));
+            const A c = va[i];
             ACC d;
-            if (AMP == FQ_AMP_INT) {
-                const double fl = floor(x);
-                const uint4 w = draw(rkey, stepno, 0xFFFFFFFEu, KeyOps<K>::rng_h(key));
-                d = (ACC)((long long)fl + (uniform53(w) < x - fl ? 1 : 0));
+            if constexpr (KIND != FQ_KIND_MOM_1D) {
+                const int s = MD::diag_index(key);
+                if constexpr (AMP == FQ_AMP_F32) {
+                    d = c + c * __ldg(R->del32 + s);
+                } else if constexpr (AMP == FQ_AMP_F64) {
+                    d = c * __ldg(R->fac64 + s);
+                } else {
+                    const double x = (double)c * __ldg(R->fac64 + s);
+                    const double fl = floor(x);
+                    const uint4 w = draw(rkey, stepno, 0xFFFFFFFEu, KeyOps<K>::rng_h(key));
+                    d = (ACC)((long long)fl + (uniform53(w) < x - fl ? 1 : 0));
+                }
             } else {
-                d = (ACC)x;
+                const double hii = MD::diagonal(R->mp, key);
+                const double S0 = R->st->shift, dt = R->st->dt;
+                if constexpr (AMP == FQ_AMP_F32) {
+                    d = c + c * (float)(dt * (S0 - hii));
+                } else if constexpr (AMP == FQ_AMP_F64) {
+                    d = c * (1.0 + dt * (S0 - hii));
+                } else {
+                    const double x = (double)c * (1.0 + dt * (S0 - hii));
+                    const double fl = floor(x);
+                    const uint4 w = draw(rkey, stepno, 0xFFFFFFFEu, KeyOps<K>::rng_h(key));
+                    d = (ACC)((long long)fl + (uniform53(w) < x - fl ? 1 : 0));
+                }
             }
-            const int q = table_insert(tkey, mask, key);
-            if (q < 0) full = true; else tacc[q] = d;
+            bool nw;
+            const int q = table_insert(tkey, mask, key, nw);
+            if (q < 0) {
+                full = true;
+                tlist[i] = 0;
+            } else {
+                tlist[i] = (unsigned short)q;
+                tacc[q] = d;
+            }
         }
         __syncthreads();
         // annihilation: every spawn to the bucket adds into its address
         for (unsigned j = tid; j < n_sp; j += BLOCK) {
             const K key = sk[j];
             const ACC v = (ACC)sv[j];
-            const int q = table_insert(tkey, mask, key);
-            if (q < 0) full = true; else acc_add(&tacc[q], v);
-        }
-        if (full) atomicOr(&st->err, FQ_DERR_TABLE);
-        __syncthreads();
-
-        // vector compression Pi on each merged value; kept values are
-        // written back so that estimator lookups see c^(n+1)
-        unsigned kept = 0;
-        double nrm = 0.0;
-        const unsigned q0 = tid * spt;
-        for (unsigned q = q0; q < q0 + spt; ++q) {
-            const K key = tkey[q];
-            if (key == EMPTY) continue;
-            const ACC w = tacc[q];
-            if (AMP == FQ_AMP_INT) {
-                if (w != 0) { ++kept; nrm += fabs((double)w); }
-            } else if (det) {
-                if (w != 0.0) { ++kept; nrm += fabs((double)w); }
-            } else {
-                const double aw = fabs((double)w);
-                double out = 0.0;
-                if (aw >= theta) {
-                    out = (double)w;
-                } else if (aw > 0.0) {
-                    const uint4 r = draw(rkey, stepno, 0xFFFFFFFFu, KeyOps<K>::rng_h(key));
-                    if (uniform53(r) < aw / theta) out = copysign(theta, (double)w);
-                }
-                if (AMP == FQ_AMP_F32) out = (double)(float)out;
-                tacc[q] = (ACC)out;
-                if (out != 0.0) { ++kept; nrm += fabs(out); }
+            bool nw;
+            const int q = table_insert(tkey, mask, key, nw);
+            if (q < 0) {
+                full = true;
+                continue;
             }
+            if (nw) tlist[atomicAdd(&s_nlist, 1u)] = (unsigned short)q;
+            acc_add(&tacc[q], v);
         }
-        unsigned total;
-        unsigned off = block_excl_scan<BLOCK>(kept, s_warp, total);
-        const bool fits = total <= Cv;
-        if (fits) {
-            for (unsigned q = q0; q < q0 + spt; ++q) {
-                const K key = tkey[q];
-                if (key == EMPTY) continue;
-                const ACC w = tacc[q];
-                if (w != (ACC)0) {
-                    ok[off] = key;
-                    oa[off] = (A)w;
-                    ++off;
+        __syncthreads();
+        const unsigned nl = s_nlist;
+
+        // Pi over the used slots; survivors leave warp by warp
+        for (unsigned base = (unsigned)warp * 32; base < nl; base += BLOCK) {
+            const unsigned i = base + lane;
+            bool keep = false;
+            ACC out = (ACC)0;
+            K key = EMPTY;
+            int q = -1;
+            if (i < nl) {
+                q = tlist[i];
+                key = tkey[q];
+                keep = compress<AMP>(tacc[q], R, rkey, stepno, KeyOps<K>::rng_h(key), out);
+                if (!keep) out = (ACC)0;
+                tacc[q] = out;
+            }
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+            unsigned pos0 = 0;
+            if (lane == 0 && bal) pos0 = atomicAdd(&s_nout, (unsigned)__popc(bal));
+            pos0 = __shfl_sync(0xFFFFFFFFu, pos0, 0);
+            if (keep) {
+                const unsigned pos = pos0 + (unsigned)__popc(bal & ((1u << lane) - 1u));
+                if (pos < Cv) {
+                    ok[pos] = key;
+                    oa[pos] = (A)out;
+                } else {
+                    over = true;
+                }
+                ++nlen;
+                if constexpr (AMP == FQ_AMP_INT) {
+                    const unsigned long long a = (unsigned long long)(out < 0 ? -out : out);
+                    add128(nlo, nhi, a, 0ull);
+                } else {
+                    if (det) {
+                        nfp += fabs((double)out);
+                    } else {
+                        unsigned long long lo, hi;
+                        fixed_of(out, nq, lo, hi, range_bad);
+                        add128(nlo, nhi, lo, hi);
+                    }
                 }
             }
         }
         __syncthreads();
         // projected-energy terms whose address falls in this bucket
-        double hp = 0.0, vp = 0.0;
         const unsigned e0 = R->ref_off[seg], e1 = R->ref_off[seg + 1];
-        const K* rk = (const K*)R->ref_keys;
-        for (unsigned e = e0 + tid; e < e1; e += BLOCK) {
-            const int q = table_find(tkey, mask, rk[e]);
-            const double cv = q >= 0 ? (double)tacc[q] : 0.0;
-            hp += R->ref_h[e] * cv;
-            vp += R->ref_v[e] * cv;
+        if (e1 > e0) {  // uniform
+            double hp = 0.0, vp = 0.0;
+            const K* rk = (const K*)R->ref_keys;
+            for (unsigned e = e0 + tid; e < e1; e += BLOCK) {
+                const int q = table_find(tkey, mask, rk[e]);
+                const double cv = q >= 0 ? (double)tacc[q] : 0.0;
+                hp += R->ref_h[e] * cv;
+                vp += R->ref_v[e] * cv;
+            }
+            const double bh = block_sum<BLOCK>(hp, s_redd);
+            const double bv = block_sum<BLOCK>(vp, s_redd);
+            if (tid == 0) {
+                R->part_h[seg] = bh;
+                R->part_v[seg] = bv;
+            }
         }
-        const double bn = block_sum<BLOCK>(nrm, s_redd);
-        const double bh = block_sum<BLOCK>(hp, s_redd);
-        const double bv = block_sum<BLOCK>(vp, s_redd);
+        // release the used slots for the next bucket
+        for (unsigned i = tid; i < nl; i += BLOCK) {
+            const unsigned q = tlist[i];
+            tkey[q] = EMPTY;
+            tacc[q] = (ACC)0;
+        }
         if (tid == 0) {
-            if (!fits) atomicOr(&st->err, FQ_DERR_VEC_CAP);
-            R->vcount[cur ^ 1][seg] = fits ? total : 0u;
-            R->part_norm[seg] = bn;
-            R->part_len[seg] = total;
-            R->part_h[seg] = bh;
-            R->part_v[seg] = bv;
+            const unsigned nout = s_nout;
+            R->vcount[cur ^ 1][seg] = nout <= Cv ? nout : Cv;
             R->sfill[seg] = 0u;
         }
         __syncthreads();
     }
+    if (R) merge_flush<BLOCK>(R, nlo, nhi, nlen, nfp, full, over, range_bad, s_red, s_redd);
+}
+
+// ---------------------------------------------------------------------------
+// diagonal factors of the coming step: 1 + dt (S - H_ii) and its FP32
+// increment, per value s = sum n(n-1) (real space, H_ii = (u/2) s)
+
+__device__ __forceinline__ void write_factors(const RunDesc* R, double S, double dt) {
+    for (int s = threadIdx.x; s <= R->smax; s += blockDim.x) {
+        const double hii = (R->mp.u * 0.5) * (double)s;
+        R->fac64[s] = 1.0 + dt * (S - hii);
+        R->del32[s] = (float)(dt * (S - hii));
+    }
+}
+
+static __global__ void k_factors(const RunDesc* __restrict__ runs) {
+    const RunDesc* R = runs + blockIdx.x;
+    if (R->smax >= 0 && R->fac64) write_factors(R, R->st->shift, R->st->dt);
 }
 
 // ---------------------------------------------------------------------------
@@ -451,58 +708,85 @@ template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_shift(const RunDesc* __restrict__ runs) {
     const RunDesc* R = runs + blockIdx.x;
     RunState* st = R->st;
-    __shared__ double s_redd[BLOCK / 32];
-    __shared__ unsigned long long s_redl[BLOCK / 32];
-    if (*(volatile unsigned*)&st->err) return;
-    double nrm = 0.0, hp = 0.0, vp = 0.0;
-    unsigned long long len = 0;
-    for (unsigned s = threadIdx.x; s < R->B; s += BLOCK) {
-        nrm += R->part_norm[s];
-        hp += R->part_h[s];
-        vp += R->part_v[s];
-        len += R->part_len[s];
+    __shared__ double s_S;
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        s_ok = 0;
+        if (!*(volatile unsigned*)&st->err) {
+            double nrm;
+            if (R->mode_det) nrm = st->norm_fp;
+            else nrm = fixed_to_double(st->norm_lo, st->norm_hi, R->norm_q);
+            const unsigned long long len = st->len_acc;
+            double hp = 0.0, vp = 0.0;
+            for (unsigned i = 0; i < R->n_ref_bkt; ++i) {
+                hp += R->part_h[R->ref_bkt[i]];
+                vp += R->part_v[R->ref_bkt[i]];
+            }
+            if (nrm == 0.0 || len == 0) {
+                st->err |= FQ_DERR_EMPTY;
+            } else {
+                const double dt = st->dt;
+                const double zd = st->zeta / dt, xd = st->xi / dt;
+                const double S1 =
+                    (st->shift - zd * log(nrm / st->norm)) - xd * log(nrm / st->target);
+                StatsRow row;
+                row.step = st->step + 1;
+                row.len = (long long)len;
+                row.exact_steps = (long long)st->n_exact;
+                row.inexact_steps = (long long)st->n_inexact;
+                row.n_spawns = (long long)st->n_spawns;
+                row.shift = S1;
+                row.norm = nrm;
+                row.hproj = hp;
+                row.vproj = vp;
+                R->hist[st->hist_head % FQ_HIST_CAP] = row;
+                st->hist_head += 1;
+                st->shift = S1;
+                st->norm = nrm;
+                st->step += 1;
+                st->len = (long long)len;
+                st->cur ^= 1;
+                st->last_hproj = hp;
+                st->last_vproj = vp;
+                st->last_exact = row.exact_steps;
+                st->last_inexact = row.inexact_steps;
+                st->last_spawns = row.n_spawns;
+                s_S = S1;
+                s_ok = 1;
+            }
+            st->n_exact = 0;
+            st->n_inexact = 0;
+            st->n_spawns = 0;
+            st->norm_lo = 0;
+            st->norm_hi = 0;
+            st->norm_fp = 0.0;
+            st->len_acc = 0;
+        }
     }
-    nrm = block_sum<BLOCK>(nrm, s_redd);
-    hp = block_sum<BLOCK>(hp, s_redd);
-    vp = block_sum<BLOCK>(vp, s_redd);
-    len = block_sum<BLOCK>(len, s_redl);
-    if (threadIdx.x != 0) return;
-    if (nrm == 0.0 || len == 0) {
-        st->err |= FQ_DERR_EMPTY;
-        return;
-    }
-    const double dt = st->dt;
-    const double zd = st->zeta / dt, xd = st->xi / dt;
-    const double S1 = (st->shift - zd * log(nrm / st->norm)) - xd * log(nrm / st->target);
-    StatsRow row;
-    row.step = st->step + 1;
-    row.len = (long long)len;
-    row.exact_steps = (long long)st->n_exact;
-    row.inexact_steps = (long long)st->n_inexact;
-    row.n_spawns = (long long)st->n_spawns;
-    row.shift = S1;
-    row.norm = nrm;
-    row.hproj = hp;
-    row.vproj = vp;
-    R->hist[st->hist_head % FQ_HIST_CAP] = row;
-    st->hist_head += 1;
-    st->shift = S1;
-    st->norm = nrm;
-    st->step += 1;
-    st->len = (long long)len;
-    st->cur ^= 1;
-    st->last_hproj = hp;
-    st->last_vproj = vp;
-    st->last_exact = row.exact_steps;
-    st->last_inexact = row.inexact_steps;
-    st->last_spawns = row.n_spawns;
-    st->n_exact = 0;
-    st->n_inexact = 0;
-    st->n_spawns = 0;
+    __syncthreads();
+    if (s_ok && R->smax >= 0 && R->fac64) write_factors(R, s_S, st->dt);
 }
 
 // ---------------------------------------------------------------------------
 // set-up and read-out helpers (not on the per-step path)
+
+// sqrt(k), -(t sqrt(k)) and its FP32 rounding for k <= kmax; m / n in FP64
+// and FP32 for 1 <= n <= m <= mmax
+static __global__ void k_tables(double t, int kmax, double* sq, double* hop, float* hop32, int mmax,
+                         double* r64, float* r32) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= kmax) {
+        const double s = sqrt((double)i);
+        sq[i] = s;
+        hop[i] = -(t * s);
+        hop32[i] = (float)hop[i];
+    }
+    if (r64 && i < (mmax + 1) * (mmax + 1)) {
+        const int m = i / (mmax + 1), n = i % (mmax + 1);
+        r64[i] = n ? (double)m / (double)n : 0.0;
+        r32[i] = n ? (float)m / (float)n : 0.0f;
+    }
+}
 
 template <class K, int AMP>
 __global__ void k_seed(const RunDesc* __restrict__ R, const K* __restrict__ keys,

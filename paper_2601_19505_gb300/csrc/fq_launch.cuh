@@ -21,7 +21,7 @@ template <class K, int AMP, int KIND> struct Launch {
     }
     static void merge(const LaunchCfg& c, const RunDesc* d, const unsigned* sr, unsigned G,
                       cudaStream_t s) {
-        const size_t smem = (size_t)c.slots * (sizeof(K) + sizeof(ACC));
+        const size_t smem = (size_t)c.slots * (sizeof(K) + sizeof(ACC) + 2);
         if (c.merge_block == 512)
             k_merge<K, AMP, KIND, 512><<<c.merge_grid, 512, smem, s>>>(d, sr, G, c.slots);
         else
@@ -86,7 +86,7 @@ template <class K, int AMP, int KIND> struct Launch {
         k.key_bytes = sizeof(K);
         k.amp_bytes = sizeof(A);
         k.spawn_bytes = sizeof(S);
-        k.acc_bytes = sizeof(ACC);
+        k.acc_bytes = sizeof(ACC) + 2;  // table slot: accumulator + list entry
         k.spawn = spawn;
         k.merge = merge;
         k.prepare = prepare;

@@ -11,9 +11,9 @@
 #define FQ_KIND_MOM_1D 3
 
 // amplitude representation
-#define FQ_AMP_INT 0  // int64 amplitudes, int32 spawns
-#define FQ_AMP_F64 1  // double amplitudes and spawns
-#define FQ_AMP_F32 2  // float amplitudes and spawns, FP64 sums
+#define FQ_AMP_INT 0  // int64 amplitudes, int32 spawns, exact integer sums
+#define FQ_AMP_F64 1  // double amplitudes and spawns, FP64 sums
+#define FQ_AMP_F32 2  // float amplitudes, spawns and sums
 
 // device-side error bits (RunState::err)
 #define FQ_DERR_SPAWN_CAP 1u
@@ -21,6 +21,7 @@
 #define FQ_DERR_TABLE 4u
 #define FQ_DERR_EMPTY 8u
 #define FQ_DERR_TIMEOUT 16u
+#define FQ_DERR_RANGE 32u  // an amplitude beyond the exact-norm range
 
 #define FQ_MAX_MOM_MODES 64
 #define FQ_HIST_CAP 65536u
@@ -31,6 +32,10 @@ struct ModelParams {
     int kind, M, N, Lx, Ly, nbits;
     double t, u;
     double g;                        // u / (2M), momentum space
+    int kmax;                        // largest index of the sqrt/hop tables
+    const double* sqrt_tab;          // sqrt((double)k), k <= kmax (device)
+    const double* hop_tab;           // -(t * sqrt((double)k)), k <= kmax (device)
+    const float* hop32_tab;          // (float) of hop_tab
     double eps[FQ_MAX_MOM_MODES];    // momentum-space single-particle energies
 };
 
@@ -41,7 +46,8 @@ struct StatsRow {
 };
 
 // Mutable per-run state in device memory.  The kernels of step n read
-// shift/norm/step/cur; the shift kernel writes the next values.
+// shift/step/cur/dt; the shift kernel writes the next values and clears
+// the accumulators of the step.
 struct RunState {
     double shift;      // S^(n)
     double norm;       // N^(n) = ||c^(n)||_1
@@ -54,14 +60,24 @@ struct RunState {
     unsigned long long hist_head;                     // rows written
     double last_hproj, last_vproj;
     long long last_exact, last_inexact, last_spawns;
+    // norm of the step in flight: exact sum in units of 2^norm_q (128-bit),
+    // or a plain FP64 sum in the deterministic limit
+    unsigned long long norm_lo, norm_hi;
+    double norm_fp;
+    unsigned long long len_acc;
 };
 
 // Everything a kernel needs to process one run's segments.  Lives in a
 // device array, one entry per run of a batch.
 struct RunDesc {
     ModelParams mp;
+    int amp;            // FQ_AMP_*
     int mode_det;       // deterministic limit: every column exact, no compression
     double theta, t_rel;
+    int theta_pow2;     // theta = 2^theta_exp: compression decided in integers
+    int theta_exp;
+    int norm_q;         // exact norm unit 2^norm_q
+    int trel_one;       // t_rel == 1
     unsigned key_x, key_y;   // Philox key
     int log2B;
     unsigned B, seg_base, Cv, Cs;
@@ -73,14 +89,20 @@ struct RunDesc {
     unsigned* sfill;
     RunState* st;
     StatsRow* hist;
+    int mmax;                 // largest m of the ratio table (real space)
+    const double* ratio64;    // (double)m / (double)n, index m * (mmax + 1) + n
+    const float* ratio32;     // (float)m / (float)n
+    int smax;                 // largest sum n(n-1) (real space)
+    double* fac64;            // 1 + dt (S - H_ii) per s = sum n(n-1), this step
+    float* del32;             // (float)(dt (S - H_ii)) per s, this step
     const void* ref_keys;     // reference terms sorted by segment
     const double* ref_h;      // y_r H_{r,j}
     const double* ref_v;      // y_r on the reference address itself, else 0
     const unsigned* ref_off;  // B + 1 offsets into the reference terms
-    double* part_norm;        // per-segment partial sums (length B)
-    double* part_h;
+    const unsigned* ref_bkt;  // segments holding reference terms, ascending
+    unsigned n_ref_bkt;
+    double* part_h;           // per-segment projected-energy partial sums
     double* part_v;
-    unsigned long long* part_len;
 };
 
 struct LaunchCfg {
