@@ -173,6 +173,11 @@ int fq_run_step(fq_run *r, int64_t n);
 /* Wait for queued work; report a device-side error (the run is rolled back
  * to its last completed step and can continue). */
 int fq_run_sync(fq_run *r);
+/* The device-side cause of the last error a synchronising call reported:
+ * bit 0 a spawn bucket, bit 1 a vector segment, bit 2 an on-chip or scratch
+ * annihilation table was full, bit 3 the population died, bit 5 an
+ * amplitude left the exact-norm range (|c| / threshold >= 2^63).  0 if none. */
+int fq_run_error_bits(const fq_run *r, unsigned *bits);
 /* Synchronise and return the row of the last completed step (step 0 after
  * seeding: len, shift and norm set, the rest 0). */
 int fq_run_stats(fq_run *r, fq_stats *out);

@@ -8,5 +8,5 @@ fallback: importing the objects works anywhere, creating a run needs a GPU.
 """
 from .fciqmc import (  # noqa: F401
     BH_MOM_1D, BH_REAL_1D, BH_REAL_2D, KEY_DTYPE, MODE_DETERMINISTIC, MODE_INT, MODE_REAL32,
-    MODE_REAL64, STATS_DTYPE, Batch, FqError, Hamiltonian, Run, default_params, keys_from_ints,
+    MODE_REAL64, STATS_DTYPE, Batch, FqError, Hamiltonian, Run, RunError, default_params, keys_from_ints,
     keys_to_ints, version)

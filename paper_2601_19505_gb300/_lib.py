@@ -61,6 +61,7 @@ SYMBOLS = {
     "fq_run_set_target": (C.c_int, [C.c_void_p, C.c_double]),
     "fq_run_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "fq_run_sync": (C.c_int, [C.c_void_p]),
+    "fq_run_error_bits": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint)]),
     "fq_run_stats": (C.c_int, [C.c_void_p, C.POINTER(FqStats)]),
     "fq_run_history": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "fq_run_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,

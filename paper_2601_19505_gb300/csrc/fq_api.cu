@@ -88,7 +88,7 @@ struct fq_run {
     int amp, det;
     const KernelSet* ks;
     int log2B;
-    unsigned B, Cv, Cs, slots;
+    unsigned B, Cv, Cs, slots;  // slots: on-chip table slots per merge warp
     RunState* st;
     StatsRow* hist;
     unsigned* vcount[2];
@@ -115,7 +115,9 @@ struct fq_run {
     fq_batch* single;
     LaunchCfg tuned;
     bool has_tuned;
+    unsigned scratch_slots;  // global scratch table size for buckets too big for SW
     unsigned gen;  // bumped whenever a device pointer of the run changes
+    unsigned last_err_bits;  // device error bits reported by the last check
     double* pinned;        // host staging slot for parameter updates
     cudaEvent_t staged;    // completes when the staged value has been copied
 };
@@ -131,6 +133,9 @@ struct fq_batch {
     cudaGraphExec_t g1, g16;
     bool owned_by_run;
     std::vector<unsigned> gens;  // run generations the descriptors were built from
+    unsigned char* scratch;      // merge scratch tables (from runs[0]'s allocator)
+    size_t scratch_bytes;
+    std::vector<LaunchCfg> shapes;  // launch shapes the scratch was sized for
 };
 
 // ---------------------------------------------------------------------------
@@ -487,22 +492,35 @@ static cudaError_t sync_self(fq_run* r) {
     return e;
 }
 
-static LaunchCfg default_cfg(const KernelSet* ks, unsigned slots, unsigned G) {
+// a launch shape: persistent grids of one (spawn) or a few (merge) blocks per
+// SM, sized by occupancy; at most one warp per segment
+static LaunchCfg make_cfg(const KernelSet* ks, int spawn_wpb, int spawn_waves, int merge_wpb,
+                          unsigned slots, unsigned G) {
     LaunchCfg c;
-    c.spawn_block = 256;
-    c.merge_block = 512;
+    c.spawn_wpb = spawn_wpb;
+    c.merge_wpb = merge_wpb;
     c.slots = slots;
+    c.scratch_slots = 0;
+    c.scratch = nullptr;
     const int sms = num_sms();
-    int occ_s = ks->spawn_occupancy(c.spawn_block);
-    const size_t smem = (size_t)slots * (ks->key_bytes + ks->acc_bytes);
-    int occ_m = ks->merge_occupancy(c.merge_block, smem);
+    int occ_s = ks->spawn_occupancy(spawn_wpb);
+    const size_t smem = (size_t)merge_wpb * slots * ks->slot_bytes;
+    int occ_m = ks->merge_occupancy(merge_wpb, smem);
     if (occ_s < 1) occ_s = 1;
     if (occ_m < 1) occ_m = 1;
-    c.spawn_grid = (int)std::min<long long>((long long)sms * occ_s, G);
-    c.merge_grid = (int)std::min<long long>((long long)sms * occ_m, G);
-    if (c.spawn_grid < 1) c.spawn_grid = 1;
-    if (c.merge_grid < 1) c.merge_grid = 1;
+    const long long ws = ((long long)G + spawn_wpb - 1) / spawn_wpb;
+    const long long wm = ((long long)G + merge_wpb - 1) / merge_wpb;
+    c.spawn_grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * occ_s * spawn_waves, ws));
+    c.merge_grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * occ_m, wm));
     return c;
+}
+
+// on-chip table slots per merge warp: 512, fewer if a warp's share of
+// shared memory would not allow two 8-warp blocks per SM
+static unsigned warp_slots(const KernelSet* ks) {
+    unsigned sw = 512;
+    while (sw > 128 && 8ull * sw * ks->slot_bytes > 110u * 1024u) sw >>= 1;
+    return sw;
 }
 
 static void batch_free(fq_batch* b);
@@ -548,19 +566,28 @@ extern "C" int fq_run_create(fq_run** out, const fq_ham* h, const fq_params* p, 
         delete r;
         return FQ_ERR_INVALID;
     }
-    const size_t kb = r->ks->key_bytes, ab = r->ks->amp_bytes, sb = r->ks->spawn_bytes,
-                 cb = r->ks->acc_bytes;
-    const unsigned max_slots = 8192;
-    double per_seg = 3000.0;
-    for (;;) {
-        const unsigned long long want = (unsigned long long)std::ceil((lcap + scap) / per_seg);
-        r->B = next_pow2(std::max<unsigned long long>(1, want));
+    const size_t kb = r->ks->key_bytes, ab = r->ks->amp_bytes, sb = r->ks->spawn_bytes;
+    // segments: at the expected steady state (len ~ target / threshold,
+    // spawns ~ len) a segment's entries plus the spawns into its bucket fill
+    // about a third of one merge warp's on-chip table
+    r->slots = warp_slots(r->ks);
+    double l_ss = std::min(p->target / th, dim), s_ss = 1.1 * l_ss;
+    if (r->det) {
+        l_ss = std::min(lcap, dim);
+        s_ss = l_ss * (double)max_offdiag(h->mp);
+    }
+    const unsigned long long want =
+        (unsigned long long)std::ceil((l_ss + s_ss) / (r->slots / 3.0));
+    r->B = next_pow2(std::max<unsigned long long>(1, std::min<unsigned long long>(want, 1ull << 28)));
+    {
+        // spawns arrive in clumps (one address receives spawns from many
+        // sources; every neighbour's in the deterministic limit), so the
+        // bucket count fluctuates like a compound Poisson sum with clump size k
         const double mv = lcap / r->B, ms = scap / r->B;
-        r->Cv = (unsigned)((mv + 5.0 * std::sqrt(mv) + 32.0 + 31.0) / 32.0) * 32u;
-        r->Cs = (unsigned)((ms + 5.0 * std::sqrt(ms) + 32.0 + 31.0) / 32.0) * 32u;
-        r->slots = std::max(512u, next_pow2((unsigned long long)std::ceil(1.15 * (r->Cv + r->Cs))));
-        if (r->slots <= max_slots) break;
-        per_seg *= 0.75;
+        const double k = r->det ? (double)max_offdiag(h->mp) : 8.0;
+        r->Cv = (unsigned)((mv + 4.0 * std::sqrt(mv) + 16.0 + 31.0) / 32.0) * 32u;
+        r->Cs = (unsigned)((ms + 4.0 * std::sqrt(ms * k) + k + 16.0 + 31.0) / 32.0) * 32u;
+        r->scratch_slots = std::max(r->slots, next_pow2((unsigned long long)std::ceil((r->Cv + r->Cs) / 0.9)));
     }
     r->log2B = ilog2(r->B);
     const unsigned B = r->B;
@@ -609,7 +636,7 @@ extern "C" int fq_run_create(fq_run** out, const fq_ham* h, const fq_params* p, 
         delete r;
         return FQ_ERR_NOMEM;
     }
-    (void)cb;
+
     RunState s0;
     memset(&s0, 0, sizeof s0);
     s0.dt = p->dt;
@@ -898,12 +925,24 @@ static void enqueue_steps(fq_batch* b, int n, cudaStream_t s) {
     }
 }
 
-static void batch_free(fq_batch* b) {
-    if (!b) return;
+static void batch_release(fq_batch* b) {
     if (b->g1) cudaGraphExecDestroy(b->g1);
     if (b->g16) cudaGraphExecDestroy(b->g16);
     if (b->d_desc) cudaFree(b->d_desc);
     if (b->d_seg_run) cudaFree(b->d_seg_run);
+    b->g1 = b->g16 = nullptr;
+    b->d_desc = nullptr;
+    b->d_seg_run = nullptr;
+}
+
+static void batch_free(fq_batch* b) {
+    if (!b) return;
+    batch_release(b);
+    if (b->scratch) {
+        fq_run* r0 = b->runs[0];
+        if (r0->has_alloc) r0->alloc.free(r0->alloc.ctx, b->scratch, b->scratch_bytes, (void*)r0->stream);
+        else cudaFreeAsync(b->scratch, r0->stream);
+    }
     delete b;
 }
 
@@ -922,29 +961,78 @@ static int capture(fq_batch* b, int n, cudaGraphExec_t* out) {
     return cuda_err(e);
 }
 
+// the launch shapes a batch may use: the default first, then the ones the
+// autotuner tries
+static std::vector<LaunchCfg> batch_shapes(fq_batch* b, unsigned slots) {
+    std::vector<LaunchCfg> v;
+    const size_t limit = 200u * 1024u;
+    v.push_back(make_cfg(b->ks, 8, 1, 8, slots, b->G));
+    for (int sw : {4, 8})
+        for (int waves : {1, 2})
+            for (int mw : {4, 8})
+                for (unsigned sl : {slots / 2, slots, slots * 2}) {
+                    if (sl < 64 || (size_t)mw * sl * b->ks->slot_bytes > limit) continue;
+                    v.push_back(make_cfg(b->ks, sw, waves, mw, sl, b->G));
+                }
+    return v;
+}
+
 static int batch_build(fq_batch* b) {
     const size_t nr = b->runs.size();
     b->gens.resize(nr);
     for (size_t i = 0; i < nr; ++i) b->gens[i] = b->runs[i]->gen;
     std::vector<RunDesc> desc(nr);
     std::vector<unsigned> seg_run;
-    unsigned base = 0, slots = 512;
+    unsigned base = 0, slots = 0, ss = 0;
     for (size_t i = 0; i < nr; ++i) {
         fq_run* r = b->runs[i];
         fill_desc(r, desc[i], base);
         for (unsigned s = 0; s < r->B; ++s) seg_run.push_back((unsigned)i);
         base += r->B;
         slots = std::max(slots, r->slots);
+        ss = std::max(ss, r->scratch_slots);
     }
     b->G = base;
     CK(cudaMalloc((void**)&b->d_desc, sizeof(RunDesc) * nr));
     CK(cudaMalloc((void**)&b->d_seg_run, sizeof(unsigned) * base));
     CK(cudaMemcpy(b->d_desc, desc.data(), sizeof(RunDesc) * nr, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(b->d_seg_run, seg_run.data(), sizeof(unsigned) * base, cudaMemcpyHostToDevice));
-    const size_t smem = (size_t)slots * (b->ks->key_bytes + b->ks->acc_bytes);
-    CK(b->ks->prepare(smem));
-    if (nr == 1 && b->runs[0]->has_tuned && b->runs[0]->tuned.slots == slots) b->cfg = b->runs[0]->tuned;
-    else b->cfg = default_cfg(b->ks, slots, b->G);
+    CK(b->ks->prepare(200u * 1024u));
+    b->shapes = batch_shapes(b, slots);
+    // scratch tables for the largest number of merge warps of any shape
+    size_t warps = 0;
+    for (const LaunchCfg& c : b->shapes) warps = std::max(warps, (size_t)c.merge_grid * c.merge_wpb);
+    const size_t bytes = warps * ss * b->ks->slot_bytes;
+    if (!b->scratch || b->scratch_bytes < bytes) {
+        fq_run* r0 = b->runs[0];
+        if (b->scratch) {
+            CK(cudaStreamSynchronize(b->stream));
+            if (r0->has_alloc) r0->alloc.free(r0->alloc.ctx, b->scratch, b->scratch_bytes, (void*)r0->stream);
+            else cudaFreeAsync(b->scratch, r0->stream);
+            b->scratch = nullptr;
+        }
+        void* p = nullptr;
+        if (r0->has_alloc) p = r0->alloc.alloc(r0->alloc.ctx, bytes, (void*)r0->stream);
+        else if (cudaMallocAsync(&p, bytes, r0->stream) != cudaSuccess) p = nullptr;
+        if (!p) return FQ_ERR_NOMEM;
+        b->scratch = (unsigned char*)p;
+        b->scratch_bytes = bytes;
+        b->ks->scratch_init(b->scratch, ss, (unsigned)warps, r0->stream);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(r0->stream));
+    }
+    for (LaunchCfg& c : b->shapes) {
+        c.scratch = b->scratch;
+        c.scratch_slots = ss;
+    }
+    b->cfg = b->shapes[0];
+    if (nr == 1 && b->runs[0]->has_tuned) {
+        const LaunchCfg& t = b->runs[0]->tuned;
+        for (const LaunchCfg& c : b->shapes)
+            if (c.spawn_wpb == t.spawn_wpb && c.spawn_grid == t.spawn_grid &&
+                c.merge_wpb == t.merge_wpb && c.merge_grid == t.merge_grid && c.slots == t.slots)
+                b->cfg = c;
+    }
     int rc = capture(b, 1, &b->g1);
     if (!rc) rc = capture(b, 16, &b->g16);
     return rc;
@@ -960,6 +1048,8 @@ static int batch_new(fq_run* const* runs, int n, bool owned, fq_batch** out) {
     b->d_desc = nullptr;
     b->d_seg_run = nullptr;
     b->g1 = b->g16 = nullptr;
+    b->scratch = nullptr;
+    b->scratch_bytes = 0;
     int rc = batch_build(b);
     if (rc) {
         batch_free(b);
@@ -974,13 +1064,7 @@ static int batch_refresh(fq_batch* b) {
     for (size_t i = 0; i < b->runs.size(); ++i) stale |= b->gens[i] != b->runs[i]->gen;
     if (!stale) return FQ_OK;
     CK(cudaStreamSynchronize(b->stream));
-    if (b->g1) cudaGraphExecDestroy(b->g1);
-    if (b->g16) cudaGraphExecDestroy(b->g16);
-    if (b->d_desc) cudaFree(b->d_desc);
-    if (b->d_seg_run) cudaFree(b->d_seg_run);
-    b->g1 = b->g16 = nullptr;
-    b->d_desc = nullptr;
-    b->d_seg_run = nullptr;
+    batch_release(b);
     return batch_build(b);
 }
 
@@ -1017,6 +1101,7 @@ static int run_check(fq_run* r) {
     unsigned err = 0;
     CK(cudaMemcpy(&err, &r->st->err, sizeof err, cudaMemcpyDeviceToHost));
     if (!err) return FQ_OK;
+    r->last_err_bits = err;
     RunState s;
     CK(cudaMemcpy(&s, r->st, sizeof s, cudaMemcpyDeviceToHost));
     s.err = 0;
@@ -1029,6 +1114,12 @@ static int run_check(fq_run* r) {
     if (err & FQ_DERR_EMPTY) return FQ_ERR_EMPTY;
     if (err & FQ_DERR_TIMEOUT) return FQ_ERR_TIMEOUT;
     return FQ_ERR_CAPACITY;
+}
+
+extern "C" int fq_run_error_bits(const fq_run* r, unsigned* bits) {
+    if (!r || !bits) return FQ_ERR_INVALID;
+    *bits = r->last_err_bits;
+    return FQ_OK;
 }
 
 extern "C" int fq_run_sync(fq_run* r) {
@@ -1168,30 +1259,13 @@ extern "C" int fq_run_spawns(fq_run* r, fq_key* dest, double* val, size_t cap, s
 
 static int autotune(fq_batch* b, int steps) {
     if (steps < 1) return FQ_ERR_INVALID;
-    const int sms = num_sms();
-    const size_t smem = (size_t)b->cfg.slots * (b->ks->key_bytes + b->ks->acc_bytes);
-    std::vector<LaunchCfg> cands;
-    for (int sb : {256, 512})
-        for (int sw : {1, 2})
-            for (int mb : {256, 512}) {
-                const int os = b->ks->spawn_occupancy(sb);
-                const int om = b->ks->merge_occupancy(mb, smem);
-                if (os < 1 || om < 1) continue;
-                LaunchCfg c = b->cfg;
-                c.spawn_block = sb;
-                c.spawn_grid = (int)std::max<long long>(
-                    1, std::min<long long>((long long)sms * os * sw / 2, b->G));
-                c.merge_block = mb;
-                c.merge_grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * om, b->G));
-                cands.push_back(c);
-            }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 1e30f;
     LaunchCfg bestc = b->cfg;
-    for (const LaunchCfg& c : cands) {
-        b->cfg = c;
+    for (size_t i = 1; i < b->shapes.size(); ++i) {
+        b->cfg = b->shapes[i];
         enqueue_steps(b, 1, b->stream);  // warm
         cudaEventRecord(e0, b->stream);
         enqueue_steps(b, steps, b->stream);
@@ -1201,7 +1275,7 @@ static int autotune(fq_batch* b, int steps) {
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms < best) {
             best = ms;
-            bestc = c;
+            bestc = b->cfg;
         }
     }
     cudaEventDestroy(e0);

@@ -91,6 +91,12 @@ template <> struct KeyOps<u128> {
     }
 };
 
+__device__ __forceinline__ int clz_k(uint64_t x) { return __clzll((long long)x); }
+__device__ __forceinline__ int clz_k(u128 x) {
+    const uint64_t hi = (uint64_t)(x >> 64);
+    return hi ? __clzll((long long)hi) : 64 + __clzll((long long)(uint64_t)x);
+}
+
 // start bit of mode s (0-based): one past the s-th separator
 template <class K> __device__ __forceinline__ int mode_start(K k, int s) {
     return s == 0 ? 0 : KeyOps<K>::nth(~k, s - 1) + 1;
@@ -212,6 +218,39 @@ template <int KIND> struct RealModel {
                                                 V& val) {
         const int d = (int)(kk / (unsigned)c.n_occ), r = (int)(kk % (unsigned)c.n_occ);
         const int P = KeyOps<K>::nth(run_starts(key), r);
+        if constexpr (KIND == FQ_KIND_REAL_1D) {
+            // a hop to a neighbouring site only moves one separator: swap
+            // the last one-bit of the run with the zero above it (+1), or the
+            // zero below the run with its first one-bit (-1); across the ring's
+            // seam the whole string shifts by one bit
+            typedef KeyOps<K> O;
+            const int nb = p.nbits;
+            const int ns = run_from(key, P);
+            int nt;
+            K dest;
+            if (d == 0) {
+                if (P + ns == nb) {  // last mode -> mode 0
+                    nt = run_from(key, 0);
+                    dest = ((key & ~O::bit(nb - 1)) << 1) | (K)1;
+                } else {
+                    nt = run_from(key, P + ns + 1);
+                    dest = key ^ ((K)3 << (P + ns - 1));
+                }
+            } else {
+                if (P == 0) {  // mode 0 -> last mode
+                    const K z = ~key & O::low(nb);
+                    nt = nb - 1 - (O::W - 1 - clz_k(z));
+                    dest = (key >> 1) | O::bit(nb - 1);
+                } else {
+                    const K z = ~key & O::low(P - 1);
+                    nt = z ? (P - 2 - (O::W - 1 - clz_k(z))) : (P - 1);
+                    dest = key ^ ((K)3 << (P - 1));
+                }
+            }
+            if constexpr (sizeof(V) == 4) val = __ldg(p.hop32_tab + ns * (nt + 1));
+            else val = __ldg(p.hop_tab + ns * (nt + 1));
+            return dest;
+        }
         const int s = P - KeyOps<K>::popc(key & KeyOps<K>::low(P));
         const int ns = run_from(key, P);
         const int s2 = neighbour(p, s, d);
@@ -221,16 +260,17 @@ template <int KIND> struct RealModel {
         else val = __ldg(p.hop_tab + ns * (nt + 1));
         return add_boson(del_bit(key, P), s2);
     }
-    // sum over modes of n (n - 1): H_ii = (u/2) times this
+    // sum over modes of n (n - 1), so H_ii = (u/2) times this: windows of
+    // w >= 2 consecutive one-bits lie inside one mode's run, and a run of n
+    // ones holds n(n-1)/2 of them
     template <class K> __device__ __forceinline__ static int diag_index(K k) {
-        K st = run_starts(k);
+        K x = k & (k >> 1);
         int s = 0;
-        while (st) {
-            const int n = run_from(k, KeyOps<K>::ctz(st));
-            s += n * (n - 1);
-            st &= st - 1;
+        while (x) {
+            s += KeyOps<K>::popc(x);
+            x &= x >> 1;
         }
-        return s;
+        return 2 * s;
     }
 };
 

@@ -48,112 +48,62 @@ template <> struct AmpT<FQ_AMP_F64> { typedef double A, S, ACC, C; };
 template <> struct AmpT<FQ_AMP_F32> { typedef float A, S, ACC, C; };
 
 // ---------------------------------------------------------------------------
-// block-wide helpers (deterministic for a fixed block size)
+// warp-level helpers
 
-template <int BLOCK>
-__device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* s_warp, unsigned& total) {
-    constexpr int NW = BLOCK / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned x = v;
+__device__ __forceinline__ unsigned warp_incl_scan(unsigned x, int lane) {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        unsigned y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        const unsigned y = __shfl_up_sync(0xFFFFFFFFu, x, o);
         if (lane >= o) x += y;
     }
-    if (lane == 31) s_warp[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        unsigned w = lane < NW ? s_warp[lane] : 0u;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned y = __shfl_up_sync(0xFFFFFFFFu, w, o);
-            if (lane >= o) w += y;
-        }
-        if (lane < NW) s_warp[lane] = w;
-    }
-    __syncthreads();
-    total = s_warp[NW - 1];
-    const unsigned r = x - v + (warp ? s_warp[warp - 1] : 0u);
-    __syncthreads();
-    return r;
+    return x;
 }
-
-template <int BLOCK, class T>
-__device__ __forceinline__ T block_sum(T v, T* s_red) {
-    constexpr int NW = BLOCK / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+template <class T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
-    if (lane == 0) s_red[warp] = v;
-    __syncthreads();
-    T r = 0;
-    if (warp == 0) {
-        r = lane < NW ? s_red[lane] : (T)0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xFFFFFFFFu, r, o);
-    }
-    __syncthreads();
-    return r;  // valid in thread 0
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
 }
-
-// exact 128-bit sum over the block; valid in thread 0
-template <int BLOCK>
-__device__ __forceinline__ void block_sum128(unsigned long long& lo, unsigned long long& hi,
-                                             unsigned long long* s_red) {
-    constexpr int NW = BLOCK / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ __forceinline__ void warp_sum128(unsigned long long& lo, unsigned long long& hi) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long l = __shfl_down_sync(0xFFFFFFFFu, lo, o);
-        const unsigned long long h = __shfl_down_sync(0xFFFFFFFFu, hi, o);
+        const unsigned long long l = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+        const unsigned long long h = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
         add128(lo, hi, l, h);
     }
-    if (lane == 0) {
-        s_red[2 * warp] = lo;
-        s_red[2 * warp + 1] = hi;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        lo = lane < NW ? s_red[2 * lane] : 0ull;
-        hi = lane < NW ? s_red[2 * lane + 1] : 0ull;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long l = __shfl_down_sync(0xFFFFFFFFu, lo, o);
-            const unsigned long long h = __shfl_down_sync(0xFFFFFFFFu, hi, o);
-            add128(lo, hi, l, h);
-        }
-    }
-    __syncthreads();
 }
-
-// contiguous range of segments for this block
-__device__ __forceinline__ void block_range(unsigned G, unsigned& g0, unsigned& g1) {
-    g0 = (unsigned)(((unsigned long long)G * blockIdx.x) / gridDim.x);
-    g1 = (unsigned)(((unsigned long long)G * (blockIdx.x + 1)) / gridDim.x);
+// contiguous range of segments for global warp w of nw
+__device__ __forceinline__ void warp_range(unsigned G, unsigned w, unsigned nw, unsigned& g0,
+                                           unsigned& g1) {
+    g0 = (unsigned)(((unsigned long long)G * w) / nw);
+    g1 = (unsigned)(((unsigned long long)G * (w + 1)) / nw);
 }
 
 // ---------------------------------------------------------------------------
-// K1: spawning
+// K1: spawning.  One warp per segment range; a segment is taken in batches
+// of up to 32 * IPT entries, each lane owning IPT consecutive entries, and
+// the batch's spawn indices are dealt round-robin to the lanes.  No block
+// barriers: warps run independently.
 
-template <class K, int AMP, int KIND, int BLOCK, int IPT>
-__global__ void __launch_bounds__(BLOCK)
+template <class K, int AMP, int KIND, int WPB, int IPT>
+__global__ void __launch_bounds__(WPB * 32)
 k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, unsigned G) {
     typedef typename AmpT<AMP>::A A;
     typedef typename AmpT<AMP>::S S;
     typedef typename AmpT<AMP>::C CO;
     typedef Model<KIND> MD;
     typedef typename MD::Col Col;
-    constexpr int CH = BLOCK * IPT;
-    __shared__ K s_key[CH];
-    __shared__ CO s_coef[CH];
-    __shared__ unsigned s_off[CH + 1];
-    __shared__ unsigned s_m[CH];
-    __shared__ unsigned s_warp[BLOCK / 32];
-    __shared__ unsigned long long s_red[BLOCK / 32];
-    __shared__ unsigned s_ctl[2];
-    const int tid = threadIdx.x;
+    constexpr int CH = 32 * IPT;
+    __shared__ K s_key[WPB][CH];
+    __shared__ CO s_coef[WPB][CH];
+    __shared__ unsigned s_off[WPB][CH + 1];
+    __shared__ unsigned s_m[WPB][CH];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    K* const wkey = s_key[wib];
+    CO* const wcoef = s_coef[wib];
+    unsigned* const woff = s_off[wib];
+    unsigned* const wm = s_m[wib];
     unsigned g0, g1;
-    block_range(G, g0, g1);
+    warp_range(G, blockIdx.x * WPB + wib, gridDim.x * WPB, g0, g1);
 
     const RunDesc* R = nullptr;
     int cur_r = -1;
@@ -162,30 +112,28 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
 
     for (unsigned g = g0; g < g1; ++g) {
         const int r = (int)seg_run[g];
-        if (r != cur_r) {  // uniform: every thread reads the same r
+        if (r != cur_r) {  // warp-uniform
             if (R) {
-                const unsigned long long e = block_sum<BLOCK>(n_ex, s_red);
-                const unsigned long long ie = block_sum<BLOCK>(n_inex, s_red);
-                const unsigned long long sp = block_sum<BLOCK>(n_sp, s_red);
-                if (tid == 0) {
-                    if (e) atomicAdd(&R->st->n_exact, e);
-                    if (ie) atomicAdd(&R->st->n_inexact, ie);
-                    if (sp) atomicAdd(&R->st->n_spawns, sp);
+                n_ex = warp_sum(n_ex);
+                n_inex = warp_sum(n_inex);
+                n_sp = warp_sum(n_sp);
+                if (lane == 0) {
+                    if (n_ex) atomicAdd(&R->st->n_exact, n_ex);
+                    if (n_inex) atomicAdd(&R->st->n_inexact, n_inex);
+                    if (n_sp) atomicAdd(&R->st->n_spawns, n_sp);
                 }
                 n_ex = n_inex = n_sp = 0;
             }
             R = runs + r;
             cur_r = r;
-            // one thread reads, all use the same values: another block may
-            // set an error bit meanwhile
-            if (tid == 0) {
-                s_ctl[0] = *(volatile unsigned*)&R->st->err;
-                s_ctl[1] = (unsigned)R->st->cur;
+            // lane 0 reads, the warp shares: another warp may set an error bit
+            unsigned e = 0, c = 0;
+            if (lane == 0) {
+                e = *(volatile unsigned*)&R->st->err;
+                c = (unsigned)R->st->cur;
             }
-            __syncthreads();
-            err = s_ctl[0];
-            cur = s_ctl[1];
-            __syncthreads();
+            err = __shfl_sync(0xFFFFFFFFu, e, 0);
+            cur = __shfl_sync(0xFFFFFFFFu, c, 0);
         }
         if (err) continue;
         const unsigned seg = g - R->seg_base;
@@ -209,27 +157,27 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
 
         for (unsigned c0 = 0; c0 < n; c0 += CH) {
             const unsigned cn = min((unsigned)CH, n - c0);
-            // stage keys and amplitudes (coalesced); amplitudes go through
-            // s_coef, overwritten by the coefficients below
+            // stage keys and amplitudes (coalesced); the amplitudes go through
+            // the coefficient slots and are overwritten below
 #pragma unroll
             for (int j = 0; j < IPT; ++j) {
-                const unsigned i = j * BLOCK + tid;
+                const unsigned i = j * 32 + lane;
                 if (i < cn) {
-                    s_key[i] = vk[c0 + i];
-                    s_coef[i] = (CO)va[c0 + i];
+                    wkey[i] = vk[c0 + i];
+                    wcoef[i] = (CO)va[c0 + i];
                 }
             }
-            __syncthreads();
+            __syncwarp();
             unsigned cnt[IPT], tsum = 0;
             CO coef[IPT];
 #pragma unroll
             for (int j = 0; j < IPT; ++j) {
-                const unsigned i = tid * IPT + j;
+                const unsigned i = lane * IPT + j;
                 unsigned c_i = 0;
                 coef[j] = (CO)0;
                 if (i < cn) {
-                    const K key = s_key[i];
-                    const CO c = s_coef[i];
+                    const K key = wkey[i];
+                    const CO c = wcoef[i];
                     Col col;
                     const unsigned m = MD::num_offdiag(mp, key, col);
                     unsigned fl, ce;
@@ -240,7 +188,7 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
                         c_i = m ? fl : 0u;
                         ++n_inex;
                         coef[j] = (CO)(dt * (double)m);
-                        s_m[i] = m | (c < (CO)0 ? 0x40000000u : 0u);
+                        wm[i] = m | (c < (CO)0 ? 0x40000000u : 0u);
                     } else {
                         bool ex;
                         if (det) ex = true;
@@ -262,98 +210,80 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
                             }
                             coef[j] = ((-(CO)dt) * ratio) * c;
                         }
-                        s_m[i] = m | (ex ? 0x80000000u : 0u);
+                        wm[i] = m | (ex ? 0x80000000u : 0u);
                     }
                 }
                 cnt[j] = c_i;
                 tsum += c_i;
             }
-            unsigned total;
-            unsigned off = block_excl_scan<BLOCK>(tsum, s_warp, total);
+            const unsigned incl = warp_incl_scan(tsum, lane);
+            const unsigned total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            unsigned off = incl - tsum;
 #pragma unroll
             for (int j = 0; j < IPT; ++j) {
-                s_off[tid * IPT + j] = off;
-                s_coef[tid * IPT + j] = coef[j];
+                woff[lane * IPT + j] = off;
+                wcoef[lane * IPT + j] = coef[j];
                 off += cnt[j];
             }
-            if (tid == 0) s_off[CH] = total;
-            __syncthreads();
+            if (lane == 31) woff[CH] = total;
+            __syncwarp();
 
-            // each thread takes a contiguous run of spawn indices
-            const unsigned q0 = (unsigned)(((unsigned long long)total * tid) / BLOCK);
-            const unsigned q1 = (unsigned)(((unsigned long long)total * (tid + 1)) / BLOCK);
-            if (q0 < q1) {
-                int i;
-                {
-                    int lo = 0, hi = CH - 1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (s_off[mid] <= q0) lo = mid; else hi = mid - 1;
-                    }
-                    i = lo;
-                }
-                K key = s_key[i];
-                CO cf = s_coef[i];
-                unsigned mm = s_m[i];
-                unsigned end_i = s_off[i + 1];
+            for (unsigned q = lane; q < total; q += 32) {
+                int i = 0;
+#pragma unroll
+                for (int step = CH / 2; step >= 1; step >>= 1)
+                    if (woff[i + step] <= q) i += step;
+                const unsigned a = q - woff[i];
+                const K key = wkey[i];
+                const CO cf = wcoef[i];
+                const unsigned mm = wm[i];
+                const unsigned m = mm & 0x3FFFFFFFu;
+                const bool ex = (AMP != FQ_AMP_INT) && (mm >> 31);
                 Col col;
                 MD::num_offdiag(mp, key, col);
-                for (unsigned q = q0; q < q1; ++q) {
-                    if (q >= end_i) {
-                        do { ++i; } while (q >= s_off[i + 1]);
-                        key = s_key[i];
-                        cf = s_coef[i];
-                        mm = s_m[i];
-                        end_i = s_off[i + 1];
-                        MD::num_offdiag(mp, key, col);
-                    }
-                    const unsigned a = q - s_off[i];
-                    const unsigned m = mm & 0x3FFFFFFFu;
-                    const bool ex = (AMP != FQ_AMP_INT) && (mm >> 31);
-                    uint4 w = make_uint4(0, 0, 0, 0);
-                    unsigned kk = a;
-                    if (!ex) {
-                        w = draw(rkey, stepno, a, KeyOps<K>::rng_h(key));
-                        kk = pick(w, m);
-                    }
-                    S val;
-                    K dest;
-                    if constexpr (AMP == FQ_AMP_INT) {
-                        double hv;
-                        dest = MD::offdiag(mp, key, col, kk, hv);
-                        const double p = fabs(hv) * cf;
-                        const double fl = floor(p);
-                        const long long nw = (long long)fl + (uniform53(w) < p - fl ? 1 : 0);
-                        if (!nw) continue;
-                        const int sg = (hv > 0.0 ? -1 : 1) * ((mm & 0x40000000u) ? -1 : 1);
-                        val = (S)(sg * nw);
-                    } else {
-                        CO hv;
-                        dest = MD::offdiag(mp, key, col, kk, hv);
-                        val = hv * cf;
-                    }
-                    ++n_sp;
-                    const unsigned b = segment_of(fmix64(KeyOps<K>::rng_h(dest)), log2B);
-                    const unsigned pos = atomicAdd(&sfill[b], 1u);
-                    if (pos < Cs) {
-                        sk[(size_t)b * Cs + pos] = dest;
-                        sv[(size_t)b * Cs + pos] = val;
-                    } else {
-                        atomicOr(&R->st->err, FQ_DERR_SPAWN_CAP);
-                    }
+                uint4 w = make_uint4(0, 0, 0, 0);
+                unsigned kk = a;
+                if (!ex) {
+                    w = draw(rkey, stepno, a, KeyOps<K>::rng_h(key));
+                    kk = pick(w, m);
+                }
+                S val;
+                K dest;
+                if constexpr (AMP == FQ_AMP_INT) {
+                    double hv;
+                    dest = MD::offdiag(mp, key, col, kk, hv);
+                    const double p = fabs(hv) * cf;
+                    const double fl = floor(p);
+                    const long long nw = (long long)fl + (uniform53(w) < p - fl ? 1 : 0);
+                    if (!nw) continue;
+                    const int sg = (hv > 0.0 ? -1 : 1) * ((mm & 0x40000000u) ? -1 : 1);
+                    val = (S)(sg * nw);
+                } else {
+                    CO hv;
+                    dest = MD::offdiag(mp, key, col, kk, hv);
+                    val = hv * cf;
+                }
+                ++n_sp;
+                const unsigned b = segment_of(fmix64(KeyOps<K>::rng_h(dest)), log2B);
+                const unsigned pos = atomicAdd(&sfill[b], 1u);
+                if (pos < Cs) {
+                    sk[(size_t)b * Cs + pos] = dest;
+                    sv[(size_t)b * Cs + pos] = val;
+                } else {
+                    atomicOr(&R->st->err, FQ_DERR_SPAWN_CAP);
                 }
             }
-            __syncthreads();
+            __syncwarp();
         }
     }
     if (R) {
-        const unsigned long long e = block_sum<BLOCK>(n_ex, s_red);
-        const unsigned long long ie = block_sum<BLOCK>(n_inex, s_red);
-        const unsigned long long sp = block_sum<BLOCK>(n_sp, s_red);
-        if (tid == 0) {
-            if (e) atomicAdd(&R->st->n_exact, e);
-            if (ie) atomicAdd(&R->st->n_inexact, ie);
-            if (sp) atomicAdd(&R->st->n_spawns, sp);
+        n_ex = warp_sum(n_ex);
+        n_inex = warp_sum(n_inex);
+        n_sp = warp_sum(n_sp);
+        if (lane == 0) {
+            if (n_ex) atomicAdd(&R->st->n_exact, n_ex);
+            if (n_inex) atomicAdd(&R->st->n_inexact, n_inex);
+            if (n_sp) atomicAdd(&R->st->n_spawns, n_sp);
         }
     }
 }
@@ -446,242 +376,285 @@ __device__ __forceinline__ bool compress(typename AmpT<AMP>::ACC w, const RunDes
     }
 }
 
-// add a block's share of one run's step totals to the run's accumulators
-template <int BLOCK>
+// add a warp's share of one run's step totals to the run's accumulators
 __device__ __forceinline__ void merge_flush(const RunDesc* R, unsigned long long nlo,
                                             unsigned long long nhi, unsigned long long nlen,
                                             double nfp, bool full, bool over, bool range_bad,
-                                            unsigned long long* s_red, double* s_redd) {
-    block_sum128<BLOCK>(nlo, nhi, s_red);
-    const unsigned long long ln = block_sum<BLOCK>(nlen, s_red);
-    const double fp = block_sum<BLOCK>(nfp, s_redd);
-    const int f = __syncthreads_or(full), o = __syncthreads_or(over),
-              b = __syncthreads_or(range_bad);
-    if (threadIdx.x == 0) {
+                                            int lane) {
+    warp_sum128(nlo, nhi);
+    nlen = warp_sum(nlen);
+    nfp = warp_sum(nfp);
+    const bool f = __any_sync(0xFFFFFFFFu, full), o = __any_sync(0xFFFFFFFFu, over),
+               b = __any_sync(0xFFFFFFFFu, range_bad);
+    if (lane == 0) {
         const unsigned long long old = atomicAdd(&R->st->norm_lo, nlo);
         atomicAdd(&R->st->norm_hi, nhi + (old + nlo < old ? 1ull : 0ull));
-        atomicAdd(&R->st->len_acc, ln);
-        if (R->mode_det) atomicAdd(&R->st->norm_fp, fp);
+        atomicAdd(&R->st->len_acc, nlen);
+        if (R->mode_det) atomicAdd(&R->st->norm_fp, nfp);
         if (f) atomicOr(&R->st->err, FQ_DERR_TABLE);
         if (o) atomicOr(&R->st->err, FQ_DERR_VEC_CAP);
         if (b) atomicOr(&R->st->err, FQ_DERR_RANGE);
     }
 }
 
-// ---------------------------------------------------------------------------
-// K4: diagonal update + annihilation + vector compression + compaction +
-//     estimator accumulation, one bucket per block iteration
+// bytes of one table slot: key, accumulator, list entry
+template <class K, int AMP> __host__ __device__ constexpr size_t slot_bytes() {
+    return sizeof(K) + sizeof(typename AmpT<AMP>::ACC) + sizeof(unsigned);
+}
 
-template <class K, int AMP, int KIND, int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
-k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, unsigned G,
-        unsigned SLOTS) {
+// per-warp totals of one run, carried across buckets
+struct MergeAcc {
+    unsigned long long nlo, nhi, nlen;
+    double nfp;
+    bool full, over, range_bad;
+};
+
+// one bucket: diagonal terms and spawns into the table (tk, ta, tl; mask + 1
+// slots, all EMPTY / 0 on entry and on return), compression, compaction,
+// estimator terms
+template <class K, int AMP, int KIND>
+__device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, unsigned cur,
+                                             unsigned n_old, unsigned n_sp, K* tk,
+                                             typename AmpT<AMP>::ACC* ta, unsigned* tl,
+                                             unsigned mask, int lane, MergeAcc& acc) {
     typedef typename AmpT<AMP>::A A;
     typedef typename AmpT<AMP>::S S;
     typedef typename AmpT<AMP>::ACC ACC;
     typedef Model<KIND> MD;
+    const K EMPTY = KeyOps<K>::empty();
+    const unsigned Cv = R->Cv;
+    const K* __restrict__ vk = (const K*)R->vkeys[cur] + (size_t)seg * Cv;
+    const A* __restrict__ va = (const A*)R->vamps[cur] + (size_t)seg * Cv;
+    K* __restrict__ ok = (K*)R->vkeys[cur ^ 1] + (size_t)seg * Cv;
+    A* __restrict__ oa = (A*)R->vamps[cur ^ 1] + (size_t)seg * Cv;
+    const K* __restrict__ sk = (const K*)R->skeys + (size_t)seg * R->Cs;
+    const S* __restrict__ sv = (const S*)R->samps + (size_t)seg * R->Cs;
+    const unsigned stepno = (unsigned)(R->st->step + 1);
+    const uint2 rkey = make_uint2(R->key_x, R->key_y);
+    const int nq = R->norm_q;
+    const int det = R->mode_det;
+
+    // diagonal term c_i (1 + dt (S - H_ii)); integer walkers round it
+    // stochastically
+    for (unsigned i = lane; i < n_old; i += 32) {
+        const K key = vk[i];
+        const A c = va[i];
+        ACC d;
+        if constexpr (KIND != FQ_KIND_MOM_1D) {
+            const int si = MD::diag_index(key);
+            if constexpr (AMP == FQ_AMP_F32) {
+                d = c + c * __ldg(R->del32 + si);
+            } else if constexpr (AMP == FQ_AMP_F64) {
+                d = c * __ldg(R->fac64 + si);
+            } else {
+                const double x = (double)c * __ldg(R->fac64 + si);
+                const double fl = floor(x);
+                const uint4 w = draw(rkey, stepno, 0xFFFFFFFEu, KeyOps<K>::rng_h(key));
+                d = (ACC)((long long)fl + (uniform53(w) < x - fl ? 1 : 0));
+            }
+        } else {
+            const double hii = MD::diagonal(R->mp, key);
+            const double S0 = R->st->shift, dt = R->st->dt;
+            if constexpr (AMP == FQ_AMP_F32) {
+                d = c + c * (float)(dt * (S0 - hii));
+            } else if constexpr (AMP == FQ_AMP_F64) {
+                d = c * (1.0 + dt * (S0 - hii));
+            } else {
+                const double x = (double)c * (1.0 + dt * (S0 - hii));
+                const double fl = floor(x);
+                const uint4 w = draw(rkey, stepno, 0xFFFFFFFEu, KeyOps<K>::rng_h(key));
+                d = (ACC)((long long)fl + (uniform53(w) < x - fl ? 1 : 0));
+            }
+        }
+        bool nw;
+        const int q = table_insert(tk, mask, key, nw);
+        if (q < 0) {
+            acc.full = true;
+            tl[i] = 0;
+        } else {
+            tl[i] = (unsigned)q;
+            ta[q] = d;
+        }
+    }
+    __syncwarp();
+    // annihilation: every spawn to the bucket adds into its address; new
+    // addresses join the list in warp order
+    unsigned nl = n_old;
+    for (unsigned j0 = 0; j0 < n_sp; j0 += 32) {
+        const unsigned j = j0 + lane;
+        bool nw = false;
+        int q = -1;
+        if (j < n_sp) {
+            q = table_insert(tk, mask, sk[j], nw);
+            if (q < 0) acc.full = true;
+            else acc_add(&ta[q], (ACC)sv[j]);
+        }
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, nw);
+        if (nw) tl[nl + __popc(bal & ((1u << lane) - 1u))] = (unsigned)q;
+        nl += __popc(bal);
+    }
+    __syncwarp();
+
+    // Pi over the used slots; survivors leave in warp order
+    unsigned nout = 0;
+    for (unsigned b0 = 0; b0 < nl; b0 += 32) {
+        const unsigned i = b0 + lane;
+        bool keep = false;
+        ACC out = (ACC)0;
+        K key = EMPTY;
+        if (i < nl) {
+            const unsigned q = tl[i];
+            key = tk[q];
+            keep = compress<AMP>(ta[q], R, rkey, stepno, KeyOps<K>::rng_h(key), out);
+            if (!keep) out = (ACC)0;
+            ta[q] = out;
+        }
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+        if (keep) {
+            const unsigned pos = nout + (unsigned)__popc(bal & ((1u << lane) - 1u));
+            if (pos < Cv) {
+                ok[pos] = key;
+                oa[pos] = (A)out;
+            } else {
+                acc.over = true;
+            }
+            ++acc.nlen;
+            if constexpr (AMP == FQ_AMP_INT) {
+                const unsigned long long av = (unsigned long long)(out < 0 ? -out : out);
+                add128(acc.nlo, acc.nhi, av, 0ull);
+            } else {
+                if (det) {
+                    acc.nfp += fabs((double)out);
+                } else {
+                    unsigned long long lo, hi;
+                    fixed_of(out, nq, lo, hi, acc.range_bad);
+                    add128(acc.nlo, acc.nhi, lo, hi);
+                }
+            }
+        }
+        nout += (unsigned)__popc(bal);
+    }
+    __syncwarp();
+    // projected-energy terms whose address falls in this bucket
+    const unsigned e0 = R->ref_off[seg], e1 = R->ref_off[seg + 1];
+    if (e1 > e0) {  // warp-uniform
+        double hp = 0.0, vp = 0.0;
+        const K* rk = (const K*)R->ref_keys;
+        for (unsigned e = e0 + lane; e < e1; e += 32) {
+            const int q = table_find(tk, mask, rk[e]);
+            const double cv = q >= 0 ? (double)ta[q] : 0.0;
+            hp += R->ref_h[e] * cv;
+            vp += R->ref_v[e] * cv;
+        }
+        hp = warp_sum(hp);
+        vp = warp_sum(vp);
+        if (lane == 0) {
+            R->part_h[seg] = hp;
+            R->part_v[seg] = vp;
+        }
+    }
+    // release the used slots for the next bucket
+    for (unsigned i = lane; i < nl; i += 32) {
+        const unsigned q = tl[i];
+        tk[q] = EMPTY;
+        ta[q] = (ACC)0;
+    }
+    if (lane == 0) {
+        R->vcount[cur ^ 1][seg] = nout <= Cv ? nout : Cv;
+        R->sfill[seg] = 0u;
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// K4: diagonal update + annihilation + vector compression + compaction +
+//     estimator accumulation.  One warp per bucket range; each warp owns an
+//     on-chip table of SW slots (keys, sums, list of used slots).  A bucket
+//     whose entries and spawns could exceed 0.7 SW uses the warp's table of
+//     SS slots in global scratch memory instead.  No block barriers.
+
+template <class K, int AMP, int KIND, int WPB>
+__global__ void __launch_bounds__(WPB * 32)
+k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, unsigned G,
+        unsigned SW, unsigned char* __restrict__ scratch, unsigned SS) {
+    typedef typename AmpT<AMP>::ACC ACC;
     extern __shared__ __align__(16) unsigned char smem[];
-    K* tkey = (K*)smem;
-    ACC* tacc = (ACC*)(smem + (size_t)SLOTS * sizeof(K));
-    unsigned short* tlist = (unsigned short*)(smem + (size_t)SLOTS * (sizeof(K) + sizeof(ACC)));
-    __shared__ unsigned long long s_red[2 * (BLOCK / 32)];
-    __shared__ double s_redd[BLOCK / 32];
-    __shared__ unsigned s_nlist, s_nout;
-    __shared__ unsigned s_ctl[2];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned mask = SLOTS - 1;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned gw = blockIdx.x * WPB + wib;
+    unsigned char* base_s = smem + (size_t)wib * SW * slot_bytes<K, AMP>();
+    unsigned char* base_g = scratch + (size_t)gw * SS * slot_bytes<K, AMP>();
+    K* const sk_s = (K*)base_s;
+    ACC* const sa_s = (ACC*)(base_s + (size_t)SW * sizeof(K));
+    unsigned* const sl_s = (unsigned*)(base_s + (size_t)SW * (sizeof(K) + sizeof(ACC)));
+    K* const sk_g = (K*)base_g;
+    ACC* const sa_g = (ACC*)(base_g + (size_t)SS * sizeof(K));
+    unsigned* const sl_g = (unsigned*)(base_g + (size_t)SS * (sizeof(K) + sizeof(ACC)));
     const K EMPTY = KeyOps<K>::empty();
 
-    for (unsigned q = tid; q < SLOTS; q += BLOCK) {
-        tkey[q] = EMPTY;
-        tacc[q] = (ACC)0;
+    for (unsigned q = lane; q < SW; q += 32) {
+        sk_s[q] = EMPTY;
+        sa_s[q] = (ACC)0;
     }
+    __syncwarp();
     unsigned g0, g1;
-    block_range(G, g0, g1);
+    warp_range(G, gw, gridDim.x * WPB, g0, g1);
 
     const RunDesc* R = nullptr;
     int cur_r = -1;
     unsigned err = 0, cur = 0;
-    unsigned long long nlo = 0, nhi = 0, nlen = 0;
-    double nfp = 0.0;
-    bool range_bad = false, full = false, over = false;
-    __syncthreads();
+    MergeAcc acc = {0, 0, 0, 0.0, false, false, false};
 
     for (unsigned g = g0; g < g1; ++g) {
         const int r = (int)seg_run[g];
-        if (r != cur_r) {  // uniform
+        if (r != cur_r) {  // warp-uniform
             if (R) {
-                merge_flush<BLOCK>(R, nlo, nhi, nlen, nfp, full, over, range_bad, s_red, s_redd);
-                nlo = nhi = nlen = 0;
-                nfp = 0.0;
-                full = over = range_bad = false;
+                merge_flush(R, acc.nlo, acc.nhi, acc.nlen, acc.nfp, acc.full, acc.over,
+                            acc.range_bad, lane);
+                acc = MergeAcc{0, 0, 0, 0.0, false, false, false};
             }
             R = runs + r;
             cur_r = r;
-            // one thread reads, all use the same values: another block may
-            // set an error bit meanwhile
-            if (tid == 0) {
-                s_ctl[0] = *(volatile unsigned*)&R->st->err;
-                s_ctl[1] = (unsigned)R->st->cur;
+            // lane 0 reads, the warp shares: another warp may set an error bit
+            unsigned e = 0, c = 0;
+            if (lane == 0) {
+                e = *(volatile unsigned*)&R->st->err;
+                c = (unsigned)R->st->cur;
             }
-            __syncthreads();
-            err = s_ctl[0];
-            cur = s_ctl[1];
-            __syncthreads();
+            err = __shfl_sync(0xFFFFFFFFu, e, 0);
+            cur = __shfl_sync(0xFFFFFFFFu, c, 0);
         }
         if (err) continue;
         const unsigned seg = g - R->seg_base;
         const unsigned n_old = R->vcount[cur][seg];
         const unsigned n_sp = R->sfill[seg];
-        const unsigned Cv = R->Cv;
-        const K* __restrict__ vk = (const K*)R->vkeys[cur] + (size_t)seg * Cv;
-        const A* __restrict__ va = (const A*)R->vamps[cur] + (size_t)seg * Cv;
-        K* __restrict__ ok = (K*)R->vkeys[cur ^ 1] + (size_t)seg * Cv;
-        A* __restrict__ oa = (A*)R->vamps[cur ^ 1] + (size_t)seg * Cv;
-        const K* __restrict__ sk = (const K*)R->skeys + (size_t)seg * R->Cs;
-        const S* __restrict__ sv = (const S*)R->samps + (size_t)seg * R->Cs;
-        const unsigned stepno = (unsigned)(R->st->step + 1);
-        const uint2 rkey = make_uint2(R->key_x, R->key_y);
-        const int nq = R->norm_q;
-        const int det = R->mode_det;
-        if (tid == 0) {
-            s_nlist = n_old;
-            s_nout = 0;
+        const unsigned long long load = (unsigned long long)n_old + n_sp;
+        if (load * 10ull <= (unsigned long long)SW * 7ull) {
+            merge_bucket<K, AMP, KIND>(R, seg, cur, n_old, n_sp, sk_s, sa_s, sl_s, SW - 1u, lane,
+                                       acc);
+        } else if (load * 10ull <= (unsigned long long)SS * 9ull) {
+            merge_bucket<K, AMP, KIND>(R, seg, cur, n_old, n_sp, sk_g, sa_g, sl_g, SS - 1u, lane,
+                                       acc);
+        } else {
+            acc.full = true;  // even the scratch table cannot hold this bucket
         }
-
-        // diagonal term c_i (1 + dt (S - H_ii)); integer walkers round it
-        // stochastically
-        for (unsigned i = tid; i < n_old; i += BLOCK) {
-            const K key = vk[i];
-            const A c = va[i];
-            ACC d;
-            if constexpr (KIND != FQ_KIND_MOM_1D) {
-                const int s = MD::diag_index(key);
-                if constexpr (AMP == FQ_AMP_F32) {
-                    d = c + c * __ldg(R->del32 + s);
-                } else if constexpr (AMP == FQ_AMP_F64) {
-                    d = c * __ldg(R->fac64 + s);
-                } else {
-                    const double x = (double)c * __ldg(R->fac64 + s);
-                    const double fl = floor(x);
-                    const uint4 w = draw(rkey, stepno, 0xFFFFFFFEu, KeyOps<K>::rng_h(key));
-                    d = (ACC)((long long)fl + (uniform53(w) < x - fl ? 1 : 0));
-                }
-            } else {
-                const double hii = MD::diagonal(R->mp, key);
-                const double S0 = R->st->shift, dt = R->st->dt;
-                if constexpr (AMP == FQ_AMP_F32) {
-                    d = c + c * (float)(dt * (S0 - hii));
-                } else if constexpr (AMP == FQ_AMP_F64) {
-                    d = c * (1.0 + dt * (S0 - hii));
-                } else {
-                    const double x = (double)c * (1.0 + dt * (S0 - hii));
-                    const double fl = floor(x);
-                    const uint4 w = draw(rkey, stepno, 0xFFFFFFFEu, KeyOps<K>::rng_h(key));
-                    d = (ACC)((long long)fl + (uniform53(w) < x - fl ? 1 : 0));
-                }
-            }
-            bool nw;
-            const int q = table_insert(tkey, mask, key, nw);
-            if (q < 0) {
-                full = true;
-                tlist[i] = 0;
-            } else {
-                tlist[i] = (unsigned short)q;
-                tacc[q] = d;
-            }
-        }
-        __syncthreads();
-        // annihilation: every spawn to the bucket adds into its address
-        for (unsigned j = tid; j < n_sp; j += BLOCK) {
-            const K key = sk[j];
-            const ACC v = (ACC)sv[j];
-            bool nw;
-            const int q = table_insert(tkey, mask, key, nw);
-            if (q < 0) {
-                full = true;
-                continue;
-            }
-            if (nw) tlist[atomicAdd(&s_nlist, 1u)] = (unsigned short)q;
-            acc_add(&tacc[q], v);
-        }
-        __syncthreads();
-        const unsigned nl = s_nlist;
-
-        // Pi over the used slots; survivors leave warp by warp
-        for (unsigned base = (unsigned)warp * 32; base < nl; base += BLOCK) {
-            const unsigned i = base + lane;
-            bool keep = false;
-            ACC out = (ACC)0;
-            K key = EMPTY;
-            int q = -1;
-            if (i < nl) {
-                q = tlist[i];
-                key = tkey[q];
-                keep = compress<AMP>(tacc[q], R, rkey, stepno, KeyOps<K>::rng_h(key), out);
-                if (!keep) out = (ACC)0;
-                tacc[q] = out;
-            }
-            const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
-            unsigned pos0 = 0;
-            if (lane == 0 && bal) pos0 = atomicAdd(&s_nout, (unsigned)__popc(bal));
-            pos0 = __shfl_sync(0xFFFFFFFFu, pos0, 0);
-            if (keep) {
-                const unsigned pos = pos0 + (unsigned)__popc(bal & ((1u << lane) - 1u));
-                if (pos < Cv) {
-                    ok[pos] = key;
-                    oa[pos] = (A)out;
-                } else {
-                    over = true;
-                }
-                ++nlen;
-                if constexpr (AMP == FQ_AMP_INT) {
-                    const unsigned long long a = (unsigned long long)(out < 0 ? -out : out);
-                    add128(nlo, nhi, a, 0ull);
-                } else {
-                    if (det) {
-                        nfp += fabs((double)out);
-                    } else {
-                        unsigned long long lo, hi;
-                        fixed_of(out, nq, lo, hi, range_bad);
-                        add128(nlo, nhi, lo, hi);
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        // projected-energy terms whose address falls in this bucket
-        const unsigned e0 = R->ref_off[seg], e1 = R->ref_off[seg + 1];
-        if (e1 > e0) {  // uniform
-            double hp = 0.0, vp = 0.0;
-            const K* rk = (const K*)R->ref_keys;
-            for (unsigned e = e0 + tid; e < e1; e += BLOCK) {
-                const int q = table_find(tkey, mask, rk[e]);
-                const double cv = q >= 0 ? (double)tacc[q] : 0.0;
-                hp += R->ref_h[e] * cv;
-                vp += R->ref_v[e] * cv;
-            }
-            const double bh = block_sum<BLOCK>(hp, s_redd);
-            const double bv = block_sum<BLOCK>(vp, s_redd);
-            if (tid == 0) {
-                R->part_h[seg] = bh;
-                R->part_v[seg] = bv;
-            }
-        }
-        // release the used slots for the next bucket
-        for (unsigned i = tid; i < nl; i += BLOCK) {
-            const unsigned q = tlist[i];
-            tkey[q] = EMPTY;
-            tacc[q] = (ACC)0;
-        }
-        if (tid == 0) {
-            const unsigned nout = s_nout;
-            R->vcount[cur ^ 1][seg] = nout <= Cv ? nout : Cv;
-            R->sfill[seg] = 0u;
-        }
-        __syncthreads();
     }
-    if (R) merge_flush<BLOCK>(R, nlo, nhi, nlen, nfp, full, over, range_bad, s_red, s_redd);
+    if (R)
+        merge_flush(R, acc.nlo, acc.nhi, acc.nlen, acc.nfp, acc.full, acc.over, acc.range_bad,
+                    lane);
+}
+
+// scratch tables start empty (keys EMPTY, sums 0); each use leaves them so
+template <class K, int AMP>
+__global__ void k_scratch_init(unsigned char* scratch, unsigned SS, unsigned nwarps) {
+    typedef typename AmpT<AMP>::ACC ACC;
+    const size_t total = (size_t)SS * nwarps;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const size_t w = i / SS, q = i % SS;
+        unsigned char* base = scratch + w * SS * slot_bytes<K, AMP>();
+        ((K*)base)[q] = KeyOps<K>::empty();
+        ((ACC*)(base + (size_t)SS * sizeof(K)))[q] = (ACC)0;
+    }
 }
 
 // ---------------------------------------------------------------------------

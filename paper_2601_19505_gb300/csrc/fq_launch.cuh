@@ -14,41 +14,47 @@ template <class K, int AMP, int KIND> struct Launch {
 
     static void spawn(const LaunchCfg& c, const RunDesc* d, const unsigned* sr, unsigned G,
                       cudaStream_t s) {
-        if (c.spawn_block == 512)
-            k_spawn<K, AMP, KIND, 512, 2><<<c.spawn_grid, 512, 0, s>>>(d, sr, G);
+        if (c.spawn_wpb == 4)
+            k_spawn<K, AMP, KIND, 4, 4><<<c.spawn_grid, 128, 0, s>>>(d, sr, G);
         else
-            k_spawn<K, AMP, KIND, 256, 4><<<c.spawn_grid, 256, 0, s>>>(d, sr, G);
+            k_spawn<K, AMP, KIND, 8, 4><<<c.spawn_grid, 256, 0, s>>>(d, sr, G);
     }
     static void merge(const LaunchCfg& c, const RunDesc* d, const unsigned* sr, unsigned G,
                       cudaStream_t s) {
-        const size_t smem = (size_t)c.slots * (sizeof(K) + sizeof(ACC) + 2);
-        if (c.merge_block == 512)
-            k_merge<K, AMP, KIND, 512><<<c.merge_grid, 512, smem, s>>>(d, sr, G, c.slots);
+        const size_t smem = (size_t)c.merge_wpb * c.slots * slot_bytes<K, AMP>();
+        if (c.merge_wpb == 4)
+            k_merge<K, AMP, KIND, 4><<<c.merge_grid, 128, smem, s>>>(d, sr, G, c.slots, c.scratch,
+                                                                      c.scratch_slots);
         else
-            k_merge<K, AMP, KIND, 256><<<c.merge_grid, 256, smem, s>>>(d, sr, G, c.slots);
+            k_merge<K, AMP, KIND, 8><<<c.merge_grid, 256, smem, s>>>(d, sr, G, c.slots, c.scratch,
+                                                                      c.scratch_slots);
     }
     static cudaError_t prepare(size_t smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_merge<K, AMP, KIND, 512>,
+        cudaError_t e = cudaFuncSetAttribute(k_merge<K, AMP, KIND, 4>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        return cudaFuncSetAttribute(k_merge<K, AMP, KIND, 256>,
+        return cudaFuncSetAttribute(k_merge<K, AMP, KIND, 8>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
-    static int spawn_occupancy(int block) {
+    static int spawn_occupancy(int wpb) {
         int n = 0;
-        if (block == 512)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spawn<K, AMP, KIND, 512, 2>, 512, 0);
+        if (wpb == 4)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spawn<K, AMP, KIND, 4, 4>, 128, 0);
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spawn<K, AMP, KIND, 256, 4>, 256, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spawn<K, AMP, KIND, 8, 4>, 256, 0);
         return n;
     }
-    static int merge_occupancy(int block, size_t smem) {
+    static int merge_occupancy(int wpb, size_t smem) {
         int n = 0;
-        if (block == 512)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_merge<K, AMP, KIND, 512>, 512, smem);
+        if (wpb == 4)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_merge<K, AMP, KIND, 4>, 128, smem);
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_merge<K, AMP, KIND, 256>, 256, smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_merge<K, AMP, KIND, 8>, 256, smem);
         return n;
+    }
+    static void scratch_init(unsigned char* scratch, unsigned slots, unsigned nwarps,
+                             cudaStream_t s) {
+        k_scratch_init<K, AMP><<<1024, 256, 0, s>>>(scratch, slots, nwarps);
     }
     static void seed(const RunDesc* d, const void* keys, const double* amps, size_t n,
                      cudaStream_t s) {
@@ -86,11 +92,12 @@ template <class K, int AMP, int KIND> struct Launch {
         k.key_bytes = sizeof(K);
         k.amp_bytes = sizeof(A);
         k.spawn_bytes = sizeof(S);
-        k.acc_bytes = sizeof(ACC) + 2;  // table slot: accumulator + list entry
+        k.slot_bytes = slot_bytes<K, AMP>();
         k.spawn = spawn;
         k.merge = merge;
         k.prepare = prepare;
         k.spawn_occupancy = spawn_occupancy;
+        k.scratch_init = scratch_init;
         k.merge_occupancy = merge_occupancy;
         k.seed = seed;
         k.gather_vec = gather_vec;

@@ -9,12 +9,14 @@
 namespace fq {
 
 struct KernelSet {
-    size_t key_bytes, amp_bytes, spawn_bytes, acc_bytes;
+    size_t key_bytes, amp_bytes, spawn_bytes;
+    size_t slot_bytes;  // one merge table slot: key, sum, list entry
     void (*spawn)(const LaunchCfg&, const RunDesc*, const unsigned*, unsigned, cudaStream_t);
     void (*merge)(const LaunchCfg&, const RunDesc*, const unsigned*, unsigned, cudaStream_t);
     cudaError_t (*prepare)(size_t merge_smem);
-    int (*spawn_occupancy)(int block);
-    int (*merge_occupancy)(int block, size_t smem);
+    int (*spawn_occupancy)(int wpb);
+    int (*merge_occupancy)(int wpb, size_t smem);
+    void (*scratch_init)(unsigned char* scratch, unsigned slots, unsigned nwarps, cudaStream_t);
     void (*seed)(const RunDesc*, const void*, const double*, size_t, cudaStream_t);
     void (*gather_vec)(const void* keys, const void* amps, unsigned cap, const unsigned* cnt,
                        const unsigned* off, unsigned B, void* okeys, double* ovals, cudaStream_t);

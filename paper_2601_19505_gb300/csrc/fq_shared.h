@@ -106,11 +106,13 @@ struct RunDesc {
 };
 
 struct LaunchCfg {
-    int spawn_block;      // threads per spawn block (256 or 512)
+    int spawn_wpb;        // warps per spawn block (4 or 8)
     int spawn_grid;       // persistent spawn blocks
-    int merge_block;      // threads per merge block
+    int merge_wpb;        // warps per merge block (4 or 8)
     int merge_grid;       // persistent merge blocks
-    unsigned slots;       // on-chip table slots per merge block (power of 2)
+    unsigned slots;       // on-chip table slots per merge warp (power of 2)
+    unsigned scratch_slots;       // global scratch table slots per merge warp
+    unsigned char* scratch;       // scratch tables, merge_grid * merge_wpb of them
 };
 
 }  // namespace fq

@@ -30,6 +30,15 @@ class FqError(RuntimeError):
         super().__init__("%s: %s (%d)" % (what, msg, code))
 
 
+class RunError(FqError):
+    """A device-side error of a run, with the cause bits of fq_run_error_bits."""
+
+    def __init__(self, code: int, what: str, bits: int):
+        super().__init__(code, what)
+        self.bits = bits
+        self.args = (self.args[0] + " [device bits 0x%x]" % bits,)
+
+
 def _check(code: int, what: str):
     if code:
         raise FqError(code, what)
@@ -182,6 +191,12 @@ class Run:
             self._lib.fq_run_destroy(self.r)
             self.r = None
 
+    def _chk(self, code: int, what: str):
+        if code:
+            b = C.c_uint()
+            self._lib.fq_run_error_bits(self.r, C.byref(b))
+            raise RunError(code, what, b.value)
+
     def __del__(self):
         self.close()
 
@@ -215,20 +230,25 @@ class Run:
     def sync(self) -> int:
         return self._lib.fq_run_sync(self.r)
 
+    def error_bits(self) -> int:
+        b = C.c_uint()
+        _check(self._lib.fq_run_error_bits(self.r, C.byref(b)), "fq_run_error_bits")
+        return b.value
+
     def stats(self) -> dict:
         s = L.FqStats()
-        _check(self._lib.fq_run_stats(self.r, C.byref(s)), "fq_run_stats")
+        self._chk(self._lib.fq_run_stats(self.r, C.byref(s)), "fq_run_stats")
         return {f: getattr(s, f) for f, _ in L.FqStats._fields_}
 
     def history(self, cap: int = 1 << 16) -> np.ndarray:
         out = np.zeros(cap, dtype=STATS_DTYPE)
         n = C.c_size_t()
-        _check(self._lib.fq_run_history(self.r, _ptr(out), cap, C.byref(n)), "fq_run_history")
+        self._chk(self._lib.fq_run_history(self.r, _ptr(out), cap, C.byref(n)), "fq_run_history")
         return out[: n.value].copy()
 
     def export(self):
         n = C.c_size_t()
-        _check(self._lib.fq_run_export(self.r, None, None, 0, C.byref(n)), "fq_run_export")
+        self._chk(self._lib.fq_run_export(self.r, None, None, 0, C.byref(n)), "fq_run_export")
         cap = n.value
         k = np.zeros(max(cap, 1), dtype=KEY_DTYPE)
         a = np.zeros(max(cap, 1))
@@ -241,7 +261,7 @@ class Run:
             cap = 1 << 22
         d = np.zeros(cap, dtype=KEY_DTYPE)
         v = np.zeros(cap)
-        _check(self._lib.fq_run_spawns(self.r, _ptr(d), _ptr(v), cap, C.byref(n)), "fq_run_spawns")
+        self._chk(self._lib.fq_run_spawns(self.r, _ptr(d), _ptr(v), cap, C.byref(n)), "fq_run_spawns")
         if n.value > cap:
             raise FqError(-3, "fq_run_spawns: %d spawns exceed the buffer" % n.value)
         return d[: n.value].copy(), v[: n.value].copy()
