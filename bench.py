@@ -425,10 +425,14 @@ def main():
     ap.add_argument("--equil", type=int, default=None)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=sorted(MODE_CODE), default=None,
+                    help="override the workload's amplitude mode (exploration only)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    cfg = W.CONFIGS[args.config]
+    cfg = dict(W.CONFIGS[args.config])
+    if args.mode:
+        cfg["mode"] = args.mode
     if args.impl == "reference":
         return reference_arm(args, cfg, args.config)
     return gpu_arm(args, cfg, args.config)

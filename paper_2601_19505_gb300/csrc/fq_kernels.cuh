@@ -85,7 +85,7 @@ __device__ __forceinline__ void warp_range(unsigned G, unsigned w, unsigned nw, 
 // barriers: warps run independently.
 
 template <class K, int AMP, int KIND, int WPB, int IPT>
-__global__ void __launch_bounds__(WPB * 32)
+__global__ void __launch_bounds__(WPB * 32, 20 / WPB)
 k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, unsigned G) {
     typedef typename AmpT<AMP>::A A;
     typedef typename AmpT<AMP>::S S;
@@ -228,49 +228,67 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
             if (lane == 31) woff[CH] = total;
             __syncwarp();
 
-            for (unsigned q = lane; q < total; q += 32) {
-                int i = 0;
+            // U spawns per lane per round: all their slot reservations are in
+            // flight together before any store waits on one
+            constexpr int U = 2;
+            for (unsigned q0 = 0; q0 < total; q0 += 32 * U) {
+                K dest[U];
+                S val[U];
+                unsigned bk[U], pos[U];
+                bool has[U];
 #pragma unroll
-                for (int step = CH / 2; step >= 1; step >>= 1)
-                    if (woff[i + step] <= q) i += step;
-                const unsigned a = q - woff[i];
-                const K key = wkey[i];
-                const CO cf = wcoef[i];
-                const unsigned mm = wm[i];
-                const unsigned m = mm & 0x3FFFFFFFu;
-                const bool ex = (AMP != FQ_AMP_INT) && (mm >> 31);
-                Col col;
-                MD::num_offdiag(mp, key, col);
-                uint4 w = make_uint4(0, 0, 0, 0);
-                unsigned kk = a;
-                if (!ex) {
-                    w = draw(rkey, stepno, a, KeyOps<K>::rng_h(key));
-                    kk = pick(w, m);
+                for (int u = 0; u < U; ++u) {
+                    const unsigned q = q0 + u * 32 + lane;
+                    has[u] = false;
+                    if (q >= total) continue;
+                    int i = 0;
+#pragma unroll
+                    for (int step = CH / 2; step >= 1; step >>= 1)
+                        if (woff[i + step] <= q) i += step;
+                    const unsigned a = q - woff[i];
+                    const K key = wkey[i];
+                    const CO cf = wcoef[i];
+                    const unsigned mm = wm[i];
+                    const unsigned m = mm & 0x3FFFFFFFu;
+                    const bool ex = (AMP != FQ_AMP_INT) && (mm >> 31);
+                    Col col;
+                    MD::num_offdiag(mp, key, col);
+                    uint4 w = make_uint4(0, 0, 0, 0);
+                    unsigned kk = a;
+                    if (!ex) {
+                        w = draw(rkey, stepno, a, KeyOps<K>::rng_h(key));
+                        kk = pick(w, m);
+                    }
+                    if constexpr (AMP == FQ_AMP_INT) {
+                        double hv;
+                        dest[u] = MD::offdiag(mp, key, col, kk, hv);
+                        const double p = fabs(hv) * cf;
+                        const double fl = floor(p);
+                        const long long nw = (long long)fl + (uniform53(w) < p - fl ? 1 : 0);
+                        if (!nw) continue;
+                        const int sg = (hv > 0.0 ? -1 : 1) * ((mm & 0x40000000u) ? -1 : 1);
+                        val[u] = (S)(sg * nw);
+                    } else {
+                        CO hv;
+                        dest[u] = MD::offdiag(mp, key, col, kk, hv);
+                        val[u] = hv * cf;
+                    }
+                    has[u] = true;
+                    bk[u] = segment_of(fmix64(KeyOps<K>::rng_h(dest[u])), log2B);
                 }
-                S val;
-                K dest;
-                if constexpr (AMP == FQ_AMP_INT) {
-                    double hv;
-                    dest = MD::offdiag(mp, key, col, kk, hv);
-                    const double p = fabs(hv) * cf;
-                    const double fl = floor(p);
-                    const long long nw = (long long)fl + (uniform53(w) < p - fl ? 1 : 0);
-                    if (!nw) continue;
-                    const int sg = (hv > 0.0 ? -1 : 1) * ((mm & 0x40000000u) ? -1 : 1);
-                    val = (S)(sg * nw);
-                } else {
-                    CO hv;
-                    dest = MD::offdiag(mp, key, col, kk, hv);
-                    val = hv * cf;
-                }
-                ++n_sp;
-                const unsigned b = segment_of(fmix64(KeyOps<K>::rng_h(dest)), log2B);
-                const unsigned pos = atomicAdd(&sfill[b], 1u);
-                if (pos < Cs) {
-                    sk[(size_t)b * Cs + pos] = dest;
-                    sv[(size_t)b * Cs + pos] = val;
-                } else {
-                    atomicOr(&R->st->err, FQ_DERR_SPAWN_CAP);
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (has[u]) pos[u] = atomicAdd(&sfill[bk[u]], 1u);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (!has[u]) continue;
+                    ++n_sp;
+                    if (pos[u] < Cs) {
+                        sk[(size_t)bk[u] * Cs + pos[u]] = dest[u];
+                        sv[(size_t)bk[u] * Cs + pos[u]] = val[u];
+                    } else {
+                        atomicOr(&R->st->err, FQ_DERR_SPAWN_CAP);
+                    }
                 }
             }
             __syncwarp();
@@ -435,10 +453,19 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
     const int det = R->mode_det;
 
     // diagonal term c_i (1 + dt (S - H_ii)); integer walkers round it
-    // stochastically
+    // stochastically.  The next entries and the first spawns are loaded
+    // before the current entry is processed.
+    K nkey = lane < n_old ? vk[lane] : EMPTY;
+    A ncv = lane < n_old ? va[lane] : (A)0;
+    K skey0 = lane < n_sp ? sk[lane] : EMPTY;
+    S sval0 = lane < n_sp ? sv[lane] : (S)0;
     for (unsigned i = lane; i < n_old; i += 32) {
-        const K key = vk[i];
-        const A c = va[i];
+        const K key = nkey;
+        const A c = ncv;
+        if (i + 32 < n_old) {
+            nkey = vk[i + 32];
+            ncv = va[i + 32];
+        }
         ACC d;
         if constexpr (KIND != FQ_KIND_MOM_1D) {
             const int si = MD::diag_index(key);
@@ -484,10 +511,16 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
         const unsigned j = j0 + lane;
         bool nw = false;
         int q = -1;
+        const K key = skey0;
+        const S v = sval0;
+        if (j + 32 < n_sp) {
+            skey0 = sk[j + 32];
+            sval0 = sv[j + 32];
+        }
         if (j < n_sp) {
-            q = table_insert(tk, mask, sk[j], nw);
+            q = table_insert(tk, mask, key, nw);
             if (q < 0) acc.full = true;
-            else acc_add(&ta[q], (ACC)sv[j]);
+            else acc_add(&ta[q], (ACC)v);
         }
         const unsigned bal = __ballot_sync(0xFFFFFFFFu, nw);
         if (nw) tl[nl + __popc(bal & ((1u << lane) - 1u))] = (unsigned)q;
@@ -574,7 +607,7 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
 //     SS slots in global scratch memory instead.  No block barriers.
 
 template <class K, int AMP, int KIND, int WPB>
-__global__ void __launch_bounds__(WPB * 32)
+__global__ void __launch_bounds__(WPB * 32, 20 / WPB)
 k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, unsigned G,
         unsigned SW, unsigned char* __restrict__ scratch, unsigned SS) {
     typedef typename AmpT<AMP>::ACC ACC;
