@@ -188,10 +188,24 @@ int fq_run_history(fq_run *r, fq_stats *out, size_t cap, size_t *n);
 /* Synchronise and copy the walker vector, sorted by address, into caller
  * buffers (*n = occupied entries; min(*n, cap) written). */
 int fq_run_export(fq_run *r, fq_key *keys, double *amps, size_t cap, size_t *n);
+/* Dict-style read (Sec. 6.3): amps[i] = the amplitude of keys[i] in the
+ * current vector, 0 when the address is not stored.  Synchronises. */
+int fq_run_lookup(fq_run *r, const fq_key *keys, size_t n, double *amps);
+/* A sample of the current vector: every entry of whole segments taken in an
+ * order shuffled by `seed`, until at least `want` entries (*n = entries
+ * sampled; min(*n, cap) written).  Synchronises. */
+int fq_run_sample(fq_run *r, uint64_t seed, size_t want, fq_key *keys, double *amps, size_t cap,
+                  size_t *n);
 /* Kernel-level check: run only the spawning stage of the next step on the
  * current vector and copy out the spawn entries (destination, value; order
  * unspecified, *n = count).  The run's state does not change. */
 int fq_run_spawns(fq_run *r, fq_key *dest, double *val, size_t cap, size_t *n);
+/* Grow the vector and spawn capacities to at least these totals (never
+ * shrinks), keeping the vector.  The usual answer to FQ_ERR_CAPACITY: the
+ * run was rolled back, so grow and step again.  Synchronises. */
+int fq_run_reserve(fq_run *r, size_t capacity_vec, size_t capacity_spawn);
+/* Current total capacities (entries of the vector, spawns per step). */
+int fq_run_capacity(const fq_run *r, size_t *capacity_vec, size_t *capacity_spawn);
 /* Time the launch shapes on the current vector and keep the fastest.  Each
  * candidate runs `steps` real steps, so the run advances. */
 int fq_run_autotune(fq_run *r, int steps);

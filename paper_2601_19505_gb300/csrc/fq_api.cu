@@ -165,6 +165,16 @@ static void* dev_alloc(fq_run* r, size_t bytes) {
     return p;
 }
 
+static void dev_free(fq_run* r, void* p) {
+    for (size_t i = 0; i < r->allocs.size(); ++i)
+        if (r->allocs[i].p == p) {
+            if (r->has_alloc) r->alloc.free(r->alloc.ctx, p, r->allocs[i].bytes, (void*)r->stream);
+            else cudaFreeAsync(p, r->stream);
+            r->allocs.erase(r->allocs.begin() + (long)i);
+            return;
+        }
+}
+
 static void dev_free_all(fq_run* r) {
     for (auto& a : r->allocs) {
         if (r->has_alloc) r->alloc.free(r->alloc.ctx, a.p, a.bytes, (void*)r->stream);
@@ -523,6 +533,14 @@ static unsigned warp_slots(const KernelSet* ks) {
     return sw;
 }
 
+// per-segment capacities for totals lcap, scap over B segments (spawns
+// arrive in clumps of up to k, see fq_run_create)
+static void segment_caps(double lcap, double scap, unsigned B, double k, unsigned& Cv, unsigned& Cs) {
+    const double mv = lcap / B, ms = scap / B;
+    Cv = (unsigned)((mv + 4.0 * std::sqrt(mv) + 16.0 + 31.0) / 32.0) * 32u;
+    Cs = (unsigned)((ms + 4.0 * std::sqrt(ms * k) + k + 16.0 + 31.0) / 32.0) * 32u;
+}
+
 static void batch_free(fq_batch* b);
 static int batch_build(fq_batch* b);
 
@@ -583,10 +601,8 @@ extern "C" int fq_run_create(fq_run** out, const fq_ham* h, const fq_params* p, 
         // spawns arrive in clumps (one address receives spawns from many
         // sources; every neighbour's in the deterministic limit), so the
         // bucket count fluctuates like a compound Poisson sum with clump size k
-        const double mv = lcap / r->B, ms = scap / r->B;
         const double k = r->det ? (double)max_offdiag(h->mp) : 8.0;
-        r->Cv = (unsigned)((mv + 4.0 * std::sqrt(mv) + 16.0 + 31.0) / 32.0) * 32u;
-        r->Cs = (unsigned)((ms + 4.0 * std::sqrt(ms * k) + k + 16.0 + 31.0) / 32.0) * 32u;
+        segment_caps(lcap, scap, r->B, k, r->Cv, r->Cs);
         r->scratch_slots = std::max(r->slots, next_pow2((unsigned long long)std::ceil((r->Cv + r->Cs) / 0.9)));
     }
     r->log2B = ilog2(r->B);
@@ -1185,7 +1201,7 @@ static int gather(fq_run* r, const void* keys, const void* vals, unsigned cap, c
     CK(cudaMalloc((void**)&d_v, sizeof(double) * T));
     CK(cudaMemcpy(d_off, off.data(), sizeof(unsigned) * (B + 1), cudaMemcpyHostToDevice));
     if (spawns) r->ks->gather_spawns(keys, vals, cap, cnt_dev, d_off, B, d_k, d_v, 0);
-    else r->ks->gather_vec(keys, vals, cap, cnt_dev, d_off, B, d_k, d_v, 0);
+    else r->ks->gather_vec(keys, vals, cap, cnt_dev, d_off, B, d_k, d_v, nullptr, 0);
     CK(cudaDeviceSynchronize());
     std::vector<unsigned char> kbuf(kb * T);
     CK(cudaMemcpy(kbuf.data(), d_k, kb * T, cudaMemcpyDeviceToHost));
@@ -1215,6 +1231,155 @@ extern "C" int fq_run_export(fq_run* r, fq_key* keys, double* amps, size_t cap, 
     }
     *n = k.size();
     return rc;
+}
+
+extern "C" int fq_run_reserve(fq_run* r, size_t capacity_vec, size_t capacity_spawn) {
+    if (!r) return FQ_ERR_INVALID;
+    int rc = run_check(r);
+    if (rc) return rc;
+    const double k = r->det ? (double)max_offdiag(r->ham.mp) : 8.0;
+    unsigned Cv, Cs;
+    segment_caps((double)capacity_vec, (double)capacity_spawn, r->B, k, Cv, Cs);
+    Cv = std::max(Cv, r->Cv);
+    Cs = std::max(Cs, r->Cs);
+    if (Cv == r->Cv && Cs == r->Cs) return FQ_OK;
+    const size_t kb = r->ks->key_bytes, ab = r->ks->amp_bytes, sb = r->ks->spawn_bytes;
+    int cur = 0;
+    CK(cudaMemcpy(&cur, &r->st->cur, sizeof cur, cudaMemcpyDeviceToHost));
+    if (Cv > r->Cv) {
+        void* nk[2] = {dev_alloc(r, kb * (size_t)r->B * Cv), dev_alloc(r, kb * (size_t)r->B * Cv)};
+        void* na[2] = {dev_alloc(r, ab * (size_t)r->B * Cv), dev_alloc(r, ab * (size_t)r->B * Cv)};
+        if (!nk[0] || !nk[1] || !na[0] || !na[1]) {
+            for (int i = 0; i < 2; ++i) {
+                if (nk[i]) dev_free(r, nk[i]);
+                if (na[i]) dev_free(r, na[i]);
+            }
+            return FQ_ERR_NOMEM;
+        }
+        r->ks->restride(r->vkeys[cur], r->vamps[cur], r->Cv, r->vcount[cur], r->B, nk[cur], na[cur],
+                        Cv, r->stream);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(r->stream));
+        for (int i = 0; i < 2; ++i) {
+            dev_free(r, r->vkeys[i]);
+            dev_free(r, r->vamps[i]);
+            r->vkeys[i] = nk[i];
+            r->vamps[i] = na[i];
+        }
+        r->Cv = Cv;
+    }
+    if (Cs > r->Cs) {
+        void* nk = dev_alloc(r, kb * (size_t)r->B * Cs);
+        void* nv = dev_alloc(r, sb * (size_t)r->B * Cs);
+        if (!nk || !nv) {
+            if (nk) dev_free(r, nk);
+            if (nv) dev_free(r, nv);
+            return FQ_ERR_NOMEM;
+        }
+        dev_free(r, r->skeys);
+        dev_free(r, r->samps);
+        r->skeys = nk;
+        r->samps = nv;
+        r->Cs = Cs;
+    }
+    r->scratch_slots = std::max(r->slots, next_pow2((unsigned long long)std::ceil((r->Cv + r->Cs) / 0.9)));
+    r->gen++;
+    CK(sync_self(r));
+    return FQ_OK;
+}
+
+extern "C" int fq_run_capacity(const fq_run* r, size_t* capacity_vec, size_t* capacity_spawn) {
+    if (!r) return FQ_ERR_INVALID;
+    if (capacity_vec) *capacity_vec = (size_t)r->B * r->Cv;
+    if (capacity_spawn) *capacity_spawn = (size_t)r->B * r->Cs;
+    return FQ_OK;
+}
+
+extern "C" int fq_run_lookup(fq_run* r, const fq_key* keys, size_t n, double* amps) {
+    if (!r || (n && (!keys || !amps))) return FQ_ERR_INVALID;
+    int rc = run_check(r);
+    if (rc) return rc;
+    if (!n) return FQ_OK;
+    const size_t kb = r->ks->key_bytes;
+    std::vector<unsigned char> kbuf;
+    pack_keys(keys, n, kb, kbuf);
+    void* d_k = nullptr;
+    double* d_a = nullptr;
+    CK(cudaMalloc(&d_k, kb * n));
+    CK(cudaMalloc((void**)&d_a, sizeof(double) * n));
+    cudaError_t e = cudaMemcpy(d_k, kbuf.data(), kb * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        r->ks->lookup(r->d_self, d_k, n, d_a, r->stream);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(amps, d_a, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    cudaFree(d_k);
+    cudaFree(d_a);
+    return cuda_err(e);
+}
+
+extern "C" int fq_run_sample(fq_run* r, uint64_t seed, size_t want, fq_key* keys, double* amps,
+                             size_t cap, size_t* n) {
+    if (!r || !n || (cap && (!keys || !amps))) return FQ_ERR_INVALID;
+    *n = 0;
+    int rc = run_check(r);
+    if (rc) return rc;
+    int cur = 0;
+    CK(cudaMemcpy(&cur, &r->st->cur, sizeof cur, cudaMemcpyDeviceToHost));
+    const unsigned B = r->B;
+    std::vector<unsigned> cnt(B);
+    CK(cudaMemcpy(cnt.data(), r->vcount[cur], sizeof(unsigned) * B, cudaMemcpyDeviceToHost));
+    // whole segments in a seeded random order until `want` entries
+    std::vector<unsigned> order(B);
+    for (unsigned b = 0; b < B; ++b) order[b] = b;
+    uint64_t x = seed;
+    for (unsigned b = B; b > 1; --b) {
+        x += 0x9E3779B97F4A7C15ull;
+        uint64_t z = x;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        std::swap(order[b - 1], order[(unsigned)(z % b)]);
+    }
+    std::vector<unsigned> segs, off(1, 0);
+    size_t tot = 0;
+    for (unsigned b = 0; b < B && tot < want; ++b) {
+        const unsigned s = order[b];
+        if (!cnt[s]) continue;
+        segs.push_back(s);
+        tot += std::min(cnt[s], r->Cv);
+        off.push_back((unsigned)tot);
+    }
+    const size_t kb = r->ks->key_bytes;
+    if (tot) {
+        unsigned *d_off = nullptr, *d_segs = nullptr;
+        void* d_k = nullptr;
+        double* d_v = nullptr;
+        CK(cudaMalloc((void**)&d_off, sizeof(unsigned) * off.size()));
+        CK(cudaMalloc((void**)&d_segs, sizeof(unsigned) * segs.size()));
+        CK(cudaMalloc(&d_k, kb * tot));
+        CK(cudaMalloc((void**)&d_v, sizeof(double) * tot));
+        CK(cudaMemcpy(d_off, off.data(), sizeof(unsigned) * off.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(d_segs, segs.data(), sizeof(unsigned) * segs.size(), cudaMemcpyHostToDevice));
+        r->ks->gather_vec(r->vkeys[cur], r->vamps[cur], r->Cv, r->vcount[cur], d_off,
+                          (unsigned)segs.size(), d_k, d_v, d_segs, 0);
+        CK(cudaDeviceSynchronize());
+        std::vector<unsigned char> kbuf(kb * tot);
+        std::vector<double> v(tot);
+        CK(cudaMemcpy(kbuf.data(), d_k, kb * tot, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(v.data(), d_v, sizeof(double) * tot, cudaMemcpyDeviceToHost));
+        cudaFree(d_off); cudaFree(d_segs); cudaFree(d_k); cudaFree(d_v);
+        const size_t w = std::min(cap, tot);
+        for (size_t i = 0; i < w; ++i) {
+            fq_key k = {0, 0};
+            memcpy(&k, kbuf.data() + i * kb, kb);
+            keys[i] = k;
+            amps[i] = v[i];
+        }
+    }
+    *n = tot;
+    return FQ_OK;
 }
 
 extern "C" int fq_run_spawns(fq_run* r, fq_key* dest, double* val, size_t cap, size_t* n) {

@@ -812,13 +812,52 @@ __global__ void k_seed(const RunDesc* __restrict__ R, const K* __restrict__ keys
     }
 }
 
+// copy each segment's entries from stride `oc` to stride `nc` (capacity growth)
+template <class K, class A>
+__global__ void k_restride(const K* __restrict__ ok, const A* __restrict__ oa, unsigned oc,
+                           const unsigned* __restrict__ cnt, unsigned B, K* __restrict__ nk,
+                           A* __restrict__ na, unsigned nc) {
+    for (unsigned b = blockIdx.x; b < B; b += gridDim.x) {
+        const unsigned n = min(cnt[b], oc);
+        for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+            nk[(size_t)b * nc + i] = ok[(size_t)b * oc + i];
+            na[(size_t)b * nc + i] = oa[(size_t)b * oc + i];
+        }
+    }
+}
+
+// amplitude of each query address in the vector (0 when absent): the
+// address's segment is scanned
+template <class K, int AMP>
+__global__ void k_lookup(const RunDesc* __restrict__ R, const K* __restrict__ q, size_t n,
+                         double* __restrict__ out) {
+    typedef typename AmpT<AMP>::A A;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int cur = R->st->cur;
+    const K key = q[i];
+    const unsigned b = segment_of(fmix64(KeyOps<K>::rng_h(key)), R->log2B);
+    const unsigned c = min(R->vcount[cur][b], R->Cv);
+    const K* vk = (const K*)R->vkeys[cur] + (size_t)b * R->Cv;
+    const A* va = (const A*)R->vamps[cur] + (size_t)b * R->Cv;
+    double v = 0.0;
+    for (unsigned j = 0; j < c; ++j)
+        if (vk[j] == key) {
+            v = (double)va[j];
+            break;
+        }
+    out[i] = v;
+}
+
 // copy segments (counts from `cnt`, offsets `off`) into dense arrays
 template <class K, class T>
 __global__ void k_gather(const K* __restrict__ keys, const T* __restrict__ vals, unsigned cap,
                          const unsigned* __restrict__ cnt, const unsigned* __restrict__ off,
-                         unsigned B, K* __restrict__ okeys, double* __restrict__ ovals) {
-    for (unsigned b = blockIdx.x; b < B; b += gridDim.x) {
-        const unsigned n = min(cnt[b], cap), o = off[b];
+                         unsigned B, K* __restrict__ okeys, double* __restrict__ ovals,
+                         const unsigned* __restrict__ segs) {
+    for (unsigned x = blockIdx.x; x < B; x += gridDim.x) {
+        const unsigned b = segs ? segs[x] : x;
+        const unsigned n = min(cnt[b], cap), o = off[x];
         for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
             okeys[o + i] = keys[(size_t)b * cap + i];
             ovals[o + i] = (double)vals[(size_t)b * cap + i];

@@ -63,15 +63,24 @@ template <class K, int AMP, int KIND> struct Launch {
     }
     static void gather_vec(const void* keys, const void* amps, unsigned cap, const unsigned* cnt,
                            const unsigned* off, unsigned B, void* okeys, double* ovals,
-                           cudaStream_t s) {
+                           const unsigned* segs, cudaStream_t s) {
         k_gather<K, A><<<B < 4096 ? B : 4096, 256, 0, s>>>((const K*)keys, (const A*)amps, cap, cnt,
-                                                           off, B, (K*)okeys, ovals);
+                                                           off, B, (K*)okeys, ovals, segs);
+    }
+    static void restride(const void* ok, const void* oa, unsigned oc, const unsigned* cnt,
+                         unsigned B, void* nk, void* na, unsigned nc, cudaStream_t s) {
+        k_restride<K, A><<<B < 8192 ? B : 8192, 128, 0, s>>>((const K*)ok, (const A*)oa, oc, cnt, B,
+                                                            (K*)nk, (A*)na, nc);
+    }
+    static void lookup(const RunDesc* d, const void* keys, size_t n, double* out, cudaStream_t s) {
+        if (!n) return;
+        k_lookup<K, AMP><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d, (const K*)keys, n, out);
     }
     static void gather_spawns(const void* keys, const void* vals, unsigned cap, const unsigned* cnt,
                               const unsigned* off, unsigned B, void* okeys, double* ovals,
                               cudaStream_t s) {
         k_gather<K, S><<<B < 4096 ? B : 4096, 256, 0, s>>>((const K*)keys, (const S*)vals, cap, cnt,
-                                                           off, B, (K*)okeys, ovals);
+                                                           off, B, (K*)okeys, ovals, nullptr);
     }
     static void column(const ModelParams& mp, const void* key, void* dest, double* val,
                        unsigned cap, double* diag, unsigned* m, cudaStream_t s) {
@@ -102,6 +111,8 @@ template <class K, int AMP, int KIND> struct Launch {
         k.seed = seed;
         k.gather_vec = gather_vec;
         k.gather_spawns = gather_spawns;
+        k.lookup = lookup;
+        k.restride = restride;
         k.column = column;
         k.ref_count = ref_count;
         k.ref_terms = ref_terms;

@@ -19,7 +19,11 @@ struct KernelSet {
     void (*scratch_init)(unsigned char* scratch, unsigned slots, unsigned nwarps, cudaStream_t);
     void (*seed)(const RunDesc*, const void*, const double*, size_t, cudaStream_t);
     void (*gather_vec)(const void* keys, const void* amps, unsigned cap, const unsigned* cnt,
-                       const unsigned* off, unsigned B, void* okeys, double* ovals, cudaStream_t);
+                       const unsigned* off, unsigned B, void* okeys, double* ovals,
+                       const unsigned* segs, cudaStream_t);
+    void (*lookup)(const RunDesc* d, const void* keys, size_t n, double* out, cudaStream_t);
+    void (*restride)(const void* ok, const void* oa, unsigned oc, const unsigned* cnt, unsigned B,
+                     void* nk, void* na, unsigned nc, cudaStream_t);
     void (*gather_spawns)(const void* keys, const void* vals, unsigned cap, const unsigned* cnt,
                           const unsigned* off, unsigned B, void* okeys, double* ovals, cudaStream_t);
     void (*column)(const ModelParams&, const void* key, void* dest, double* val, unsigned cap,

@@ -255,6 +255,24 @@ class Run:
         _check(self._lib.fq_run_export(self.r, _ptr(k), _ptr(a), cap, C.byref(n)), "fq_run_export")
         return k[: n.value].copy(), a[: n.value].copy()
 
+    def lookup(self, keys) -> np.ndarray:
+        """Amplitudes of the given addresses (0 when not stored)."""
+        k = _as_keys(keys)
+        out = np.zeros(max(len(k), 1))
+        self._chk(self._lib.fq_run_lookup(self.r, _ptr(k), len(k), _ptr(out)), "fq_run_lookup")
+        return out[: len(k)].copy()
+
+    def sample(self, want: int, seed: int = 0):
+        """Entries of randomly chosen whole segments, at least `want` of them."""
+        cap = int(want) + 4 * 4096
+        k = np.zeros(cap, dtype=KEY_DTYPE)
+        a = np.zeros(cap)
+        n = C.c_size_t()
+        self._chk(self._lib.fq_run_sample(self.r, int(seed), int(want), _ptr(k), _ptr(a), cap,
+                                          C.byref(n)), "fq_run_sample")
+        m = min(n.value, cap)
+        return k[:m].copy(), a[:m].copy()
+
     def spawns(self, cap: int | None = None):
         n = C.c_size_t()
         if cap is None:
@@ -268,6 +286,37 @@ class Run:
 
     def autotune(self, steps: int = 3):
         _check(self._lib.fq_run_autotune(self.r, int(steps)), "fq_run_autotune")
+
+    def reserve(self, capacity_vec: int, capacity_spawn: int):
+        _check(self._lib.fq_run_reserve(self.r, int(capacity_vec), int(capacity_spawn)),
+               "fq_run_reserve")
+
+    def capacity(self):
+        v, s = C.c_size_t(), C.c_size_t()
+        _check(self._lib.fq_run_capacity(self.r, C.byref(v), C.byref(s)), "fq_run_capacity")
+        return v.value, s.value
+
+    def advance(self, n: int, chunk: int = 200, grow: float = 1.5, max_grows: int = 12):
+        """Step until n more steps are done.  Every `chunk` steps the run is
+        synchronised; after a capacity error (the run is rolled back to its
+        last completed step) both capacities grow by `grow` and stepping goes on."""
+        target = self.stats()["step"] + int(n)
+        grows = 0
+        while True:
+            done = self.stats()["step"]
+            if done >= target:
+                return grows
+            self.step(min(chunk, target - done))
+            rc = self.sync()
+            if rc == -3 and grows < max_grows:
+                v, s = self.capacity()
+                if self._alloc is not None:
+                    # hand cached blocks back to the driver before the copy
+                    self._alloc.torch.cuda.empty_cache()
+                self.reserve(int(v * grow), int(s * grow))
+                grows += 1
+            elif rc:
+                raise RunError(rc, "advance", self.error_bits())
 
     def profile(self, n: int):
         """Mean ms per step of (spawn, merge, shift) over n eagerly launched steps."""

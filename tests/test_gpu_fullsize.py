@@ -1,0 +1,214 @@
+"""Parity at the benchmark configurations' full sizes (needs a GB300).
+
+A full-size step holds up to 1e9 entries, beyond what the oracle can redo
+whole.  The oracle instead recomputes single outputs: for each sampled
+address j it needs only c^(n) on j and on the column of j (the only sources
+that can spawn to j, H being symmetric), which the test reads from the GPU
+vector before the step (fq_run_lookup).  Properties that hold at any size
+are checked on the full vector where it can be exported.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.blocking as BL
+import oracle.ed as ED
+import workloads as W
+from gpu_helpers import assert_same_vector, fq
+
+pytestmark = pytest.mark.gpu
+
+MODE = {"INT": 0, "REAL64": 1, "REAL32": 2}
+
+
+@pytest.fixture(autouse=True)
+def _release_device_memory():
+    """Full-size runs hold tens of GB: hand them back between tests."""
+    yield
+    import gc
+
+    import torch
+    gc.collect()
+    torch.cuda.empty_cache()
+
+
+def _make(cfg, **over):
+    c = dict(cfg)
+    c.update(over)
+    h = fq().Hamiltonian(c["kind"], c["Lx"], c["Ly"], c["N"], c["t"], c["u"])
+    m = O.Model(c["kind"], c["Lx"], c["Ly"], c["N"], c["t"], c["u"])
+    gp = fq().default_params(mode=MODE[c["mode"]], dt=c["dt"], target=c["target"],
+                             seed=c["seed"], run_id=c.get("run_id", 0),
+                             capacity_vec=int(c.get("capacity_vec", 0)),
+                             capacity_spawn=int(c.get("capacity_spawn", 0)))
+    op = O.default_params(mode=MODE[c["mode"]], dt=c["dt"], target=c["target"],
+                          seed=c["seed"], run_id=c.get("run_id", 0))
+    return h, m, gp, op
+
+
+def _sampled_parity(g, m, op, n_src, n_cand, seed, rtol):
+    """One GPU step checked on n_cand sampled outputs recomputed by the oracle."""
+    st0 = g.stats()
+    src_k, _ = g.sample(n_src, seed=seed)
+    src = fq().keys_to_ints(src_k)
+    rng = np.random.default_rng(seed)
+    cand = set(rng.choice(src, min(len(src), n_cand // 2), replace=False).tolist())
+    for k in rng.choice(src, min(len(src), n_cand // 8), replace=False):
+        nb = m.column(int(k))[0]
+        cand.update(rng.choice(nb, min(len(nb), 4), replace=False).tolist())
+    cand = sorted(int(c) for c in cand)
+    need = set(cand)
+    for j in cand:
+        need.update(m.column(j)[0])
+    need = sorted(need)
+    amps = g.lookup(fq().keys_from_ints(need))
+    g.step(1)
+    st1 = g.stats()
+    got = g.lookup(fq().keys_from_ints(cand))
+    o = O.Run(m, op)
+    nz = np.flatnonzero(amps)
+    o.seed([need[i] for i in nz], amps[nz], st0["shift"], st0["step"])
+    bad = []
+    for j, gv in zip(cand, got):
+        _, want = o.point(j)
+        if rtol == 0.0:
+            ok = gv == want
+        else:
+            ok = (gv == 0.0) == (want == 0.0) and abs(gv - want) <= rtol * abs(want)
+        if not ok:
+            bad.append((j, gv, want))
+    assert not bad, "%d of %d outputs differ, e.g. %s" % (len(bad), len(cand), bad[:3])
+    assert sum(1 for v in got if v != 0.0) > 0
+    return st0, st1
+
+
+def test_c1_integer_walkers_full_run_bit_exact():
+    """Configuration c1 in full: 2000 integer-walker steps identical to the
+    oracle, every row of the time series included."""
+    cfg = W.CONFIGS["c1"]
+    h, m, gp, op = _make(cfg)
+    g = fq().Run(h, gp)
+    g.seed_default(W.START_WEIGHT)
+    o = O.start_run(m, op, weight=W.START_WEIGHT)
+    g.step(cfg["steps"])
+    o.step(cfg["steps"])
+    assert_same_vector(g.export(), o.export(), rtol=0.0, what="c1 after %d steps" % cfg["steps"])
+    gh, oh = g.history(), o.history()
+    assert len(gh) == cfg["steps"]
+    for f in ("step", "len", "exact_steps", "inexact_steps", "n_spawns"):
+        assert np.array_equal(gh[f], oh[f]), f
+    assert np.array_equal(gh["norm"], oh["norm"])  # integer sums: exact
+    assert np.allclose(gh["shift"], oh["shift"], rtol=1e-12, atol=1e-12)
+    assert np.allclose(gh["hproj"], oh["hproj"], rtol=1e-12, atol=1e-12)
+
+
+def test_c1_energy_within_two_sigma_of_exact_diagonalisation():
+    cfg = W.CONFIGS["c1"]
+    h, m, gp, op = _make(cfg)
+    g = fq().Run(h, gp)
+    g.seed_default(W.START_WEIGHT)
+    g.step(40000)
+    hist = g.history()
+    e0 = ED.lowest(m, 1)[0]
+    r = BL.ratio_of_means(list(hist["hproj"][4000:]), list(hist["vproj"][4000:]))
+    s = BL.blocking_analysis(list(hist["shift"][4000:]))
+    assert abs(r["ratio"] - e0) < 2 * r["err"], (r, e0)
+    assert abs(s["mean"] - e0) < 2 * s["err"], (s, e0)
+
+
+def test_c2_full_size():
+    """c2 at full size (N_t = 1e7, ~1e7 occupied configurations) in the launch
+    shape the benchmark uses (autotuned)."""
+    cfg = W.CONFIGS["c2"]
+    h, m, gp, op = _make(cfg)
+    g = fq().Run(h, gp)
+    g.seed_default(W.START_WEIGHT)
+    g.step(2000)
+    g.stats()
+    g.autotune(2)
+    st0, st1 = _sampled_parity(g, m, op, n_src=3000, n_cand=3000, seed=1, rtol=1e-12)
+    assert st1["len"] > 5e6
+    keys, amps = g.export()
+    assert len(keys) == st1["len"]
+    # the one-norm is the exact sum of the stored amplitudes, rounded once
+    assert O.exact_norm(amps, 1.0, O.MODE_REAL64) == st1["norm"]
+    assert np.all(np.abs(amps) >= 1.0)
+    lo = keys["lo"]
+    assert np.all(lo < (1 << m.nbits))
+    ones = np.zeros(len(lo), dtype=np.int64)
+    x = lo.copy()
+    while np.any(x):
+        ones += (x & 1).astype(np.int64)
+        x >>= np.uint64(1)
+    assert np.all(ones == m.N)
+    assert np.all(np.diff(lo.astype(np.float64)) > 0) or len(np.unique(lo)) == len(lo)
+
+
+def _grow_to_target(g, max_steps, chunk=2):
+    """Step until the one-norm first reaches the target population."""
+    st = g.stats()
+    while st["norm"] < g.params.target and st["step"] < max_steps:
+        g.advance(chunk)
+        st = g.stats()
+    return st
+
+
+def test_c3_momentum_full_size():
+    """c3: momentum space 32/32 (63-bit addresses), N_t = 1e8, FP32 walkers.
+    The step is checked when the population first reaches N_t, before the
+    sign-problem overshoot (several times N_t) that follows."""
+    cfg = W.CONFIGS["c3"]
+    h, m, gp, op = _make(cfg)
+    g = fq().Run(h, gp)
+    try:
+        g.seed_default(W.START_WEIGHT)
+        st = _grow_to_target(g, 400)
+        assert st["norm"] >= cfg["target"] and st["len"] > 5e7, st
+        _sampled_parity(g, m, op, n_src=500, n_cand=160, seed=2, rtol=1e-5)
+    finally:
+        g.close()
+
+
+def test_c5_two_dimensional_full_size():
+    """c5: 2D 8x8, N = 64 (127-bit addresses), N_t = 5e8, FP32 walkers."""
+    cfg = W.CONFIGS["c5"]
+    h, m, gp, op = _make(cfg)
+    g = fq().Run(h, gp)
+    try:
+        g.seed_default(W.START_WEIGHT)
+        g.advance(300)
+        st = g.stats()
+        assert st["len"] > 1e7
+        _sampled_parity(g, m, op, n_src=2000, n_cand=300, seed=3, rtol=1e-5)
+    finally:
+        g.close()
+
+
+def test_c4_batch_matches_single_runs():
+    """c4: 64 runs of different sizes in one launch per kernel per step give the
+    runs' own results (draws are keyed by run id); a few are checked against
+    the same runs stepped alone and against the oracle."""
+    cfgs = W.batch_configs(64, seed=1)
+    runs = []
+    for c in cfgs:
+        h, m, gp, op = _make(c)
+        r = fq().Run(h, gp)
+        r.seed_default(W.START_WEIGHT)
+        runs.append((h, m, gp, op, r))
+    b = fq().Batch([x[4] for x in runs])
+    b.step(200)
+    b.sync()
+    for idx in (0, 17, 40, 63):
+        h, m, gp, op, r = runs[idx]
+        alone = fq().Run(h, gp)
+        alone.seed_default(W.START_WEIGHT)
+        alone.step(200)
+        (ka, aa), (kb, ab) = alone.export(), r.export()
+        assert np.array_equal(ka, kb), idx
+        assert np.allclose(aa, ab, rtol=1e-5, atol=0), idx
+        ha, hb = alone.history(), r.history()
+        assert np.array_equal(ha["len"], hb["len"])
+        _sampled_parity(r, m, op, n_src=400, n_cand=200, seed=idx, rtol=1e-5)
+    assert all(x[4].stats()["len"] > 100 for x in runs)

@@ -24,6 +24,8 @@ CONFIGS = {
                steps=2000, seed=1),
     "c2": dict(kind=1, Lx=20, Ly=1, N=20, t=1.0, u=2.0, mode="REAL64", target=1e7, dt=1e-3,
                steps=10000, seed=1),
+    # momentum space has positive off-diagonal elements (a sign problem): the
+    # population overshoots the target several-fold before the shift controls it
     "c3": dict(kind=3, Lx=32, Ly=1, N=32, t=1.0, u=4.0, mode="REAL32", target=1e8, dt=5e-4,
                steps=5000, seed=1),
     "c5": dict(kind=2, Lx=8, Ly=8, N=64, t=1.0, u=8.0, mode="REAL32", target=5e8, dt=2e-4,
