@@ -57,8 +57,10 @@ enum { FQ_BH_REAL_1D = 1, FQ_BH_REAL_2D = 2, FQ_BH_MOM_1D = 3 };
 
 /* Walker representation.  INT: integer walkers (int64 amplitudes, the
  * original integer-coefficient formulation).  REAL64: FP64 amplitudes with
- * matrix and vector compression (Sec. 3.2).  REAL32: amplitudes and spawns
- * stored in FP32, every sum and estimator in FP64.  DETERMINISTIC: no
+ * matrix and vector compression (Sec. 3.2).  REAL32: amplitudes, spawns and
+ * the per-entry arithmetic (spawn values, diagonal update, annihilation sums)
+ * in FP32; the one-norm is an exact sum rounded once to FP64, and the shift
+ * and projected-energy sums are FP64.  DETERMINISTIC: no
  * compression at all, the power iteration of Eq. fciqmc (FP64). */
 enum { FQ_MODE_INT = 0, FQ_MODE_REAL64 = 1, FQ_MODE_REAL32 = 2, FQ_MODE_DETERMINISTIC = 3 };
 

@@ -52,11 +52,14 @@ def test_deterministic_limit_is_power_iteration(kind, Lx, N, u):
         T = _dense_T(m, keys, H, dt, S_now)
 
 
+@pytest.mark.parametrize("model", [(O.REAL_1D, 5, 1, 5, 4.0), (O.MOM_1D, 6, 1, 5, 4.0),
+                                   (O.REAL_2D, 3, 3, 4, 3.0)], ids=["real1d", "mom1d", "real2d"])
 @pytest.mark.parametrize("mode", [O.MODE_REAL64, O.MODE_REAL32, O.MODE_INT])
-def test_one_step_is_unbiased(mode):
+def test_one_step_is_unbiased(mode, model):
     """E[c^(n+1)] = (1 + dt (S - H)) c^(n) for the compressed step, averaged
     over independently keyed draws (here: different step counters)."""
-    m = O.Model(O.REAL_1D, 5, 1, 5, 1.0, 4.0)
+    kind, Lx, Ly, N, u = model
+    m = O.Model(kind, Lx, Ly, N, 1.0, u)
     basis, H = ED.dense_hamiltonian(m)
     keys = ED.basis_ints(basis)
     index = {k: i for i, k in enumerate(keys)}
@@ -203,12 +206,14 @@ def _run_energy(m, params, steps, skip, seed_weight=10.0):
     return shift, proj, h
 
 
-def test_real64_run_matches_exact_energy():
-    """Sec. 4 example: 6/6, u = 6, default parameters, 3000 steps, skip 1000."""
+@pytest.mark.parametrize("mode", [O.MODE_REAL64, O.MODE_REAL32])
+def test_real_run_matches_exact_energy(mode):
+    """Sec. 4 example: 6/6, u = 6, default parameters, 3000 steps, skip 1000
+    (FP64 amplitudes, and FP32 amplitudes with FP64 estimators)."""
     g = golden("energies.json")
     m = O.Model(O.REAL_1D, 6, 1, 6, 1.0, 6.0)
     e0 = ED.lowest(m, 1)[0]
-    shift, proj, h = _run_energy(m, O.default_params(), 3000, 1000)
+    shift, proj, h = _run_energy(m, O.default_params(mode=mode), 3000, 1000)
     assert abs(shift["mean"] - e0) < 2 * shift["err"]
     assert abs(proj["ratio"] - e0) < 2 * proj["err"]
     # the paper's printed estimates, as context: same ballpark error bars
