@@ -145,6 +145,23 @@ int fq_decode(const fq_ham *h, fq_key key, uint8_t *occ);
 int fq_ham_column(const fq_ham *h, fq_key key, double *diag, fq_key *dest, double *val,
                   size_t cap, size_t *m);
 
+/* fq_ham_column without any allocation (the paper has no counterpart: this
+ * is a library-level variant).  The column is evaluated into one fixed
+ * device array of 729,600 bytes that exists from the moment the library is
+ * loaded, so the call works when device memory is exhausted (cudaMalloc
+ * would fail) and never waits for the whole device (as cudaFree does).
+ * Same arguments and results as fq_ham_column, with these limits:
+ *  - columns longer than FQ_COLUMN_NOALLOC_MAX entries are rejected with
+ *    FQ_ERR_CAPACITY, *m still set to the column's length; nothing else is
+ *    written;
+ *  - the array is shared per device: calls that overlap in time (several
+ *    host threads) race on it, so callers must serialise them;
+ *  - the first call on a device looks up the array's address and may load
+ *    the module: make it outside any CUDA stream capture. */
+#define FQ_COLUMN_NOALLOC_MAX 16384
+int fq_ham_column_noalloc(const fq_ham *h, fq_key key, double *diag, fq_key *dest, double *val,
+                          size_t cap, size_t *m);
+
 /* Create a run: device buffers sized from the parameters, all on `stream`
  * (a cudaStream_t; NULL = legacy default stream).  `alloc` may be NULL. */
 int fq_run_create(fq_run **out, const fq_ham *h, const fq_params *p, void *stream,

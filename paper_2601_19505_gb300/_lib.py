@@ -49,6 +49,8 @@ SYMBOLS = {
     "fq_decode": (C.c_int, [C.c_void_p, FqKey, C.c_void_p]),
     "fq_ham_column": (C.c_int, [C.c_void_p, FqKey, C.POINTER(C.c_double), C.c_void_p,
                                 C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "fq_ham_column_noalloc": (C.c_int, [C.c_void_p, FqKey, C.POINTER(C.c_double), C.c_void_p,
+                                        C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "fq_run_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_void_p, C.POINTER(FqParams),
                                 C.c_void_p, C.POINTER(FqAllocator)]),
     "fq_run_destroy": (None, [C.c_void_p]),

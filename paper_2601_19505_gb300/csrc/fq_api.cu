@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -1541,3 +1542,123 @@ extern "C" int fq_batch_autotune(fq_batch* b, int steps) {
     if (rc) return rc;
     return fq_batch_sync(b);
 }
+
+// ---------------------------------------------------------------------------
+// fq_ham_column_noalloc: the column of H without allocating anything.
+//
+// fq_ham_column allocates its device buffers with cudaMalloc and releases
+// them with cudaFree on every call.  Two kinds of caller cannot afford that:
+// a caller whose device memory is all taken (a large run plus a caching
+// allocator that keeps its freed blocks can leave cudaMalloc nothing), and a
+// caller with steps queued on other streams, because cudaFree waits for the
+// whole device and so stalls them.  This variant evaluates the column into
+// one fixed device array that exists from the moment the library is loaded.
+//
+// Limits and rules of use:
+//  - The array holds the matrix-element tables for N <= 128 and at most
+//    FQ_COLUMN_NOALLOC_MAX (16384) off-diagonal entries; a longer column is
+//    rejected with FQ_ERR_CAPACITY (its length is still reported).
+//  - Nothing in the array has to start at zero: every call writes the
+//    tables, the diagonal, the count and the entries before reading them.
+//  - The array is shared by every caller on a device.  Calls that overlap in
+//    time (from several host threads) race on it; callers must serialise.
+//  - The first call on a device looks up the array's device address
+//    (cudaGetSymbolAddress), which may load the module: make that first call
+//    outside any stream capture.
+
+namespace {
+constexpr unsigned kNaMax = FQ_COLUMN_NOALLOC_MAX;  // column entries
+constexpr size_t kNaTab = 129u * 130u + 1u;                   // (N+1)(N+2)+1, N <= 128
+constexpr size_t na_round(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t kNaOffSq = 0;
+constexpr size_t kNaOffHop = kNaOffSq + na_round(sizeof(double) * kNaTab);
+constexpr size_t kNaOffHop32 = kNaOffHop + na_round(sizeof(double) * kNaTab);
+constexpr size_t kNaOffHead = kNaOffHop32 + na_round(sizeof(float) * kNaTab);  // diag, m
+constexpr size_t kNaOffDest = kNaOffHead + 256;
+constexpr size_t kNaOffVal = kNaOffDest + na_round(sizeof(fq_key) * kNaMax);
+constexpr size_t kNaBytes = kNaOffVal + na_round(sizeof(double) * kNaMax);  // 729,600 B
+constexpr int kNaDevices = 64;
+std::atomic<unsigned char*> g_na_base[kNaDevices];
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_na_scratch[kNaBytes];
+
+// k_column with its tables and outputs in the fixed array: the block fills
+// the sqrt / hop tables (the expressions of k_tables), then one thread
+// enumerates the column and writes it in fq_key layout
+template <class K, int KIND>
+__global__ void __launch_bounds__(256) k_column_fixed(ModelParams mp, K key, unsigned char* base) {
+    double* sq = (double*)(base + kNaOffSq);
+    double* hop = (double*)(base + kNaOffHop);
+    float* hop32 = (float*)(base + kNaOffHop32);
+    for (int i = threadIdx.x; i <= mp.kmax; i += blockDim.x) {
+        const double s = sqrt((double)i);
+        sq[i] = s;
+        hop[i] = -(mp.t * s);
+        hop32[i] = (float)hop[i];
+    }
+    __syncthreads();
+    if (threadIdx.x) return;
+    mp.sqrt_tab = sq;
+    mp.hop_tab = hop;
+    mp.hop32_tab = hop32;
+    typedef Model<KIND> MD;
+    typename MD::Col col;
+    const unsigned m = MD::num_offdiag(mp, key, col);
+    *(double*)(base + kNaOffHead) = MD::diagonal(mp, key);
+    *(unsigned*)(base + kNaOffHead + 8) = m;
+    unsigned long long* dest = (unsigned long long*)(base + kNaOffDest);
+    double* val = (double*)(base + kNaOffVal);
+    for (unsigned k = 0; k < m && k < kNaMax; ++k) {
+        const K d = MD::offdiag(mp, key, col, k, val[k]);
+        dest[2 * k] = (unsigned long long)d;
+        dest[2 * k + 1] = sizeof(K) > 8 ? (unsigned long long)(d >> 32 >> 32) : 0ull;
+    }
+}
+
+template <class K>
+static void launch_column_fixed(int kind, const ModelParams& mp, K key, unsigned char* base) {
+    if (kind == FQ_BH_REAL_1D) k_column_fixed<K, FQ_KIND_REAL_1D><<<1, 256>>>(mp, key, base);
+    else if (kind == FQ_BH_REAL_2D) k_column_fixed<K, FQ_KIND_REAL_2D><<<1, 256>>>(mp, key, base);
+    else k_column_fixed<K, FQ_KIND_MOM_1D><<<1, 256>>>(mp, key, base);
+}
+
+extern "C" int fq_ham_column_noalloc(const fq_ham* h, fq_key key, double* diag, fq_key* dest,
+                                     double* val, size_t cap, size_t* m_out) {
+    if (!h || !key_valid(h, key)) return FQ_ERR_INVALID;
+    ModelParams mp = h->mp;
+    mp.kmax = (mp.N + 1) * (mp.N + 2);
+    if ((size_t)mp.kmax + 1 > kNaTab) return FQ_ERR_INVALID;
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_err(e);
+    if (dev < 0 || dev >= kNaDevices) return FQ_ERR_INVALID;
+    unsigned char* base = g_na_base[dev].load();
+    if (!base) {  // once per device, with that device current
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_na_scratch);
+        if (e != cudaSuccess) return cuda_err(e);
+        base = (unsigned char*)p;
+        g_na_base[dev].store(base);
+    }
+    if (h->kw == 1) launch_column_fixed<uint64_t>(mp.kind, mp, (uint64_t)key.lo, base);
+    else launch_column_fixed<u128>(mp.kind, mp, ((u128)key.hi << 64) | (u128)key.lo, base);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    unsigned char head[16];
+    if (e == cudaSuccess) e = cudaMemcpy(head, base + kNaOffHead, sizeof head, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_err(e);
+    double d;
+    unsigned m;
+    memcpy(&d, head, sizeof d);
+    memcpy(&m, head + 8, sizeof m);
+    if (m_out) *m_out = m;
+    if (m > kNaMax) return FQ_ERR_CAPACITY;  // longer than the fixed array holds
+    if (diag) *diag = d;
+    const size_t nw = std::min<size_t>(m, cap);
+    if (nw && dest) e = cudaMemcpy(dest, base + kNaOffDest, sizeof(fq_key) * nw, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && nw && val)
+        e = cudaMemcpy(val, base + kNaOffVal, sizeof(double) * nw, cudaMemcpyDeviceToHost);
+    return cuda_err(e);
+}
+static_assert(kNaBytes == 729600, "fixed column array size as documented in fciqmc.h");
