@@ -427,9 +427,68 @@ struct MergeAcc {
     bool full, over, range_bad;
 };
 
-// one bucket: diagonal terms and spawns into the table (tk, ta, tl; mask + 1
-// slots, all EMPTY / 0 on entry and on return), compression, compaction,
-// estimator terms
+// a table sum that an entry of c^(n) has taken over (no valid sum has these
+// bits: a NaN payload, or the most negative integer)
+template <class ACC> __device__ __forceinline__ ACC taken_mark();
+template <> __device__ __forceinline__ double taken_mark<double>() {
+    return __longlong_as_double(0x7FF4C0DEC0DEC0DEll);
+}
+template <> __device__ __forceinline__ float taken_mark<float>() { return __int_as_float(0x7FA0C0DE); }
+template <> __device__ __forceinline__ long long taken_mark<long long>() {
+    return (long long)0x8000000000000000ull;
+}
+__device__ __forceinline__ bool is_taken(double x) {
+    return __double_as_longlong(x) == 0x7FF4C0DEC0DEC0DEll;
+}
+__device__ __forceinline__ bool is_taken(float x) { return __float_as_int(x) == 0x7FA0C0DE; }
+__device__ __forceinline__ bool is_taken(long long x) {
+    return x == (long long)0x8000000000000000ull;
+}
+
+// Pi, compaction and the norm terms of one merged value, for a warp of lanes
+// (keep: the lane has a value)
+template <class K, int AMP>
+__device__ __forceinline__ void merge_emit(const RunDesc* R, bool has, K key,
+                                           typename AmpT<AMP>::ACC w, uint2 rkey, unsigned stepno,
+                                           K* __restrict__ ok, typename AmpT<AMP>::A* __restrict__ oa,
+                                           unsigned Cv, int nq, int det, int lane, unsigned& nout,
+                                           MergeAcc& acc) {
+    typedef typename AmpT<AMP>::ACC ACC;
+    typedef typename AmpT<AMP>::A A;
+    ACC out = (ACC)0;
+    const bool keep = has && compress<AMP>(w, R, rkey, stepno, KeyOps<K>::rng_h(key), out);
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+    if (keep) {
+        const unsigned pos = nout + (unsigned)__popc(bal & ((1u << lane) - 1u));
+        if (pos < Cv) {
+            ok[pos] = key;
+            oa[pos] = (A)out;
+        } else {
+            acc.over = true;
+        }
+        ++acc.nlen;
+        if constexpr (AMP == FQ_AMP_INT) {
+            const unsigned long long av = (unsigned long long)(out < 0 ? -out : out);
+            add128(acc.nlo, acc.nhi, av, 0ull);
+        } else {
+            if (det) {
+                acc.nfp += fabs((double)out);
+            } else {
+                unsigned long long lo, hi;
+                fixed_of(out, nq, lo, hi, acc.range_bad);
+                add128(acc.nlo, acc.nhi, lo, hi);
+            }
+        }
+    }
+    nout += (unsigned)__popc(bal);
+}
+
+// One bucket.  The spawns go into the table (tk, ta, tl; mask + 1 slots, all
+// EMPTY / 0 on entry and on return), which sums them per address.  Then each
+// entry of c^(n)'s segment, with its diagonal term, takes over the sum of
+// its own address (if any) and is compressed and compacted; then the
+// addresses that only spawns reached.  Last, the projected-energy terms of
+// the bucket's addresses.
 template <class K, int AMP, int KIND>
 __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, unsigned cur,
                                              unsigned n_old, unsigned n_sp, K* tk,
@@ -452,135 +511,121 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
     const int nq = R->norm_q;
     const int det = R->mode_det;
 
-    // diagonal term c_i (1 + dt (S - H_ii)); integer walkers round it
-    // stochastically.  The next entries and the first spawns are loaded
-    // before the current entry is processed.
-    K nkey = lane < n_old ? vk[lane] : EMPTY;
-    A ncv = lane < n_old ? va[lane] : (A)0;
-    K skey0 = lane < n_sp ? sk[lane] : EMPTY;
-    S sval0 = lane < n_sp ? sv[lane] : (S)0;
-    for (unsigned i = lane; i < n_old; i += 32) {
-        const K key = nkey;
-        const A c = ncv;
-        if (i + 32 < n_old) {
-            nkey = vk[i + 32];
-            ncv = va[i + 32];
-        }
-        ACC d;
-        if constexpr (KIND != FQ_KIND_MOM_1D) {
-            const int si = MD::diag_index(key);
-            if constexpr (AMP == FQ_AMP_F32) {
-                d = c + c * __ldg(R->del32 + si);
-            } else if constexpr (AMP == FQ_AMP_F64) {
-                d = c * __ldg(R->fac64 + si);
-            } else {
-                const double x = (double)c * __ldg(R->fac64 + si);
-                const double fl = floor(x);
-                const uint4 w = draw(rkey, stepno, 0xFFFFFFFEu, KeyOps<K>::rng_h(key));
-                d = (ACC)((long long)fl + (uniform53(w) < x - fl ? 1 : 0));
-            }
-        } else {
-            const double hii = MD::diagonal(R->mp, key);
-            const double S0 = R->st->shift, dt = R->st->dt;
-            if constexpr (AMP == FQ_AMP_F32) {
-                d = c + c * (float)(dt * (S0 - hii));
-            } else if constexpr (AMP == FQ_AMP_F64) {
-                d = c * (1.0 + dt * (S0 - hii));
-            } else {
-                const double x = (double)c * (1.0 + dt * (S0 - hii));
-                const double fl = floor(x);
-                const uint4 w = draw(rkey, stepno, 0xFFFFFFFEu, KeyOps<K>::rng_h(key));
-                d = (ACC)((long long)fl + (uniform53(w) < x - fl ? 1 : 0));
-            }
-        }
-        bool nw;
-        const int q = table_insert(tk, mask, key, nw);
-        if (q < 0) {
-            acc.full = true;
-            tl[i] = 0;
-        } else {
-            tl[i] = (unsigned)q;
-            ta[q] = d;
-        }
-    }
-    __syncwarp();
     // annihilation: every spawn to the bucket adds into its address; new
-    // addresses join the list in warp order
-    unsigned nl = n_old;
-    for (unsigned j0 = 0; j0 < n_sp; j0 += 32) {
-        const unsigned j = j0 + lane;
-        bool nw = false;
-        int q = -1;
-        const K key = skey0;
-        const S v = sval0;
-        if (j + 32 < n_sp) {
-            skey0 = sk[j + 32];
-            sval0 = sv[j + 32];
+    // addresses join the list in warp order.  The next spawns are loaded
+    // before the current ones are inserted.
+    unsigned nl = 0;
+    {
+        K skey = lane < n_sp ? sk[lane] : EMPTY;
+        S sval = lane < n_sp ? sv[lane] : (S)0;
+        for (unsigned j0 = 0; j0 < n_sp; j0 += 32) {
+            const unsigned j = j0 + lane;
+            bool nw = false;
+            int q = -1;
+            const K key = skey;
+            const S v = sval;
+            if (j + 32 < n_sp) {
+                skey = sk[j + 32];
+                sval = sv[j + 32];
+            }
+            if (j < n_sp) {
+                q = table_insert(tk, mask, key, nw);
+                if (q < 0) acc.full = true;
+                else acc_add(&ta[q], (ACC)v);
+            }
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, nw);
+            if (nw) tl[nl + __popc(bal & ((1u << lane) - 1u))] = (unsigned)q;
+            nl += __popc(bal);
         }
-        if (j < n_sp) {
-            q = table_insert(tk, mask, key, nw);
-            if (q < 0) acc.full = true;
-            else acc_add(&ta[q], (ACC)v);
-        }
-        const unsigned bal = __ballot_sync(0xFFFFFFFFu, nw);
-        if (nw) tl[nl + __popc(bal & ((1u << lane) - 1u))] = (unsigned)q;
-        nl += __popc(bal);
     }
     __syncwarp();
 
-    // Pi over the used slots; survivors leave in warp order
+    // c^(n)'s entries: diagonal term c_i (1 + dt (S - H_ii)) (integer walkers
+    // round it stochastically) plus the spawns to i, then Pi
     unsigned nout = 0;
+    {
+        K nkey = lane < n_old ? vk[lane] : EMPTY;
+        A ncv = lane < n_old ? va[lane] : (A)0;
+        for (unsigned i0 = 0; i0 < n_old; i0 += 32) {
+            const unsigned i = i0 + lane;
+            const K key = nkey;
+            const A c = ncv;
+            if (i + 32 < n_old) {
+                nkey = vk[i + 32];
+                ncv = va[i + 32];
+            }
+            ACC w = (ACC)0;
+            const bool has = i < n_old;
+            if (has) {
+                if constexpr (KIND != FQ_KIND_MOM_1D) {
+                    const int si = MD::diag_index(key);
+                    if constexpr (AMP == FQ_AMP_F32) {
+                        w = c + c * __ldg(R->del32 + si);
+                    } else if constexpr (AMP == FQ_AMP_F64) {
+                        w = c * __ldg(R->fac64 + si);
+                    } else {
+                        const double x = (double)c * __ldg(R->fac64 + si);
+                        const double fl = floor(x);
+                        const uint4 r4 = draw(rkey, stepno, 0xFFFFFFFEu, KeyOps<K>::rng_h(key));
+                        w = (ACC)((long long)fl + (uniform53(r4) < x - fl ? 1 : 0));
+                    }
+                } else {
+                    const double hii = MD::diagonal(R->mp, key);
+                    const double S0 = R->st->shift, dt = R->st->dt;
+                    if constexpr (AMP == FQ_AMP_F32) {
+                        w = c + c * (float)(dt * (S0 - hii));
+                    } else if constexpr (AMP == FQ_AMP_F64) {
+                        w = c * (1.0 + dt * (S0 - hii));
+                    } else {
+                        const double x = (double)c * (1.0 + dt * (S0 - hii));
+                        const double fl = floor(x);
+                        const uint4 r4 = draw(rkey, stepno, 0xFFFFFFFEu, KeyOps<K>::rng_h(key));
+                        w = (ACC)((long long)fl + (uniform53(r4) < x - fl ? 1 : 0));
+                    }
+                }
+                if (n_sp) {
+                    const int q = table_find(tk, mask, key);
+                    if (q >= 0) {
+                        w = w + ta[q];
+                        ta[q] = taken_mark<ACC>();
+                    }
+                }
+            }
+            merge_emit<K, AMP>(R, has, key, w, rkey, stepno, ok, oa, Cv, nq, det, lane, nout, acc);
+        }
+    }
+    __syncwarp();
+    // addresses only spawns reached
     for (unsigned b0 = 0; b0 < nl; b0 += 32) {
         const unsigned i = b0 + lane;
-        bool keep = false;
-        ACC out = (ACC)0;
+        bool has = false;
+        ACC w = (ACC)0;
         K key = EMPTY;
         if (i < nl) {
             const unsigned q = tl[i];
+            w = ta[q];
+            has = !is_taken(w);
             key = tk[q];
-            keep = compress<AMP>(ta[q], R, rkey, stepno, KeyOps<K>::rng_h(key), out);
-            if (!keep) out = (ACC)0;
-            ta[q] = out;
         }
-        const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
-        if (keep) {
-            const unsigned pos = nout + (unsigned)__popc(bal & ((1u << lane) - 1u));
-            if (pos < Cv) {
-                ok[pos] = key;
-                oa[pos] = (A)out;
-            } else {
-                acc.over = true;
-            }
-            ++acc.nlen;
-            if constexpr (AMP == FQ_AMP_INT) {
-                const unsigned long long av = (unsigned long long)(out < 0 ? -out : out);
-                add128(acc.nlo, acc.nhi, av, 0ull);
-            } else {
-                if (det) {
-                    acc.nfp += fabs((double)out);
-                } else {
-                    unsigned long long lo, hi;
-                    fixed_of(out, nq, lo, hi, acc.range_bad);
-                    add128(acc.nlo, acc.nhi, lo, hi);
-                }
-            }
-        }
-        nout += (unsigned)__popc(bal);
+        merge_emit<K, AMP>(R, has, key, w, rkey, stepno, ok, oa, Cv, nq, det, lane, nout, acc);
     }
     __syncwarp();
-    // projected-energy terms whose address falls in this bucket
+    // projected-energy terms whose address falls in this bucket: read the
+    // survivors back (this warp wrote them)
     const unsigned e0 = R->ref_off[seg], e1 = R->ref_off[seg + 1];
     if (e1 > e0) {  // warp-uniform
-        double hp = 0.0, vp = 0.0;
         const K* rk = (const K*)R->ref_keys;
-        for (unsigned e = e0 + lane; e < e1; e += 32) {
-            const int q = table_find(tk, mask, rk[e]);
-            const double cv = q >= 0 ? (double)ta[q] : 0.0;
+        const unsigned nw = nout <= Cv ? nout : Cv;
+        double hp = 0.0, vp = 0.0;
+        for (unsigned e = e0; e < e1; ++e) {
+            const K want = rk[e];
+            double cv = 0.0;
+            for (unsigned i = lane; i < nw; i += 32)
+                if (ok[i] == want) cv = (double)oa[i];
+            cv = warp_sum(cv);  // at most one lane holds the address
             hp += R->ref_h[e] * cv;
             vp += R->ref_v[e] * cv;
         }
-        hp = warp_sum(hp);
-        vp = warp_sum(vp);
         if (lane == 0) {
             R->part_h[seg] = hp;
             R->part_v[seg] = vp;
@@ -603,8 +648,8 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
 // K4: diagonal update + annihilation + vector compression + compaction +
 //     estimator accumulation.  One warp per bucket range; each warp owns an
 //     on-chip table of SW slots (keys, sums, list of used slots).  A bucket
-//     whose entries and spawns could exceed 0.7 SW uses the warp's table of
-//     SS slots in global scratch memory instead.  No block barriers.
+//     whose spawns could exceed 0.7 SW uses the warp's table of SS slots in
+//     global scratch memory instead.  No block barriers.
 
 template <class K, int AMP, int KIND, int WPB>
 __global__ void __launch_bounds__(WPB * 32, 20 / WPB)
@@ -660,7 +705,8 @@ k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
         const unsigned seg = g - R->seg_base;
         const unsigned n_old = R->vcount[cur][seg];
         const unsigned n_sp = R->sfill[seg];
-        const unsigned long long load = (unsigned long long)n_old + n_sp;
+        // the table holds the bucket's spawned addresses only
+        const unsigned long long load = n_sp;
         if (load * 10ull <= (unsigned long long)SW * 7ull) {
             merge_bucket<K, AMP, KIND>(R, seg, cur, n_old, n_sp, sk_s, sa_s, sl_s, SW - 1u, lane,
                                        acc);
