@@ -587,8 +587,8 @@ extern "C" int fq_run_create(fq_run** out, const fq_ham* h, const fq_params* p, 
     }
     const size_t kb = r->ks->key_bytes, ab = r->ks->amp_bytes, sb = r->ks->spawn_bytes;
     // segments: at the expected steady state (len ~ target / threshold,
-    // spawns ~ len) a segment's entries plus the spawns into its bucket fill
-    // about a third of one merge warp's on-chip table
+    // spawns ~ len) the spawns into a bucket fill about a third of one merge
+    // warp's on-chip table (the table holds spawned addresses only)
     r->slots = warp_slots(r->ks);
     double l_ss = std::min(p->target / th, dim), s_ss = 1.1 * l_ss;
     if (r->det) {
@@ -596,7 +596,7 @@ extern "C" int fq_run_create(fq_run** out, const fq_ham* h, const fq_params* p, 
         s_ss = l_ss * (double)max_offdiag(h->mp);
     }
     const unsigned long long want =
-        (unsigned long long)std::ceil((l_ss + s_ss) / (r->slots / 3.0));
+        (unsigned long long)std::ceil(s_ss / (r->slots / 3.0));
     r->B = next_pow2(std::max<unsigned long long>(1, std::min<unsigned long long>(want, 1ull << 28)));
     {
         // spawns arrive in clumps (one address receives spawns from many

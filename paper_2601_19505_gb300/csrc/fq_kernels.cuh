@@ -47,6 +47,11 @@ template <> struct AmpT<FQ_AMP_INT> {
 template <> struct AmpT<FQ_AMP_F64> { typedef double A, S, ACC, C; };
 template <> struct AmpT<FQ_AMP_F32> { typedef float A, S, ACC, C; };
 
+// resident blocks per SM the spawn and merge kernels are compiled for: 8-warp
+// blocks get up to 128 registers a thread (16 warps per SM), 4-warp blocks
+// up to 80 (24 warps per SM); the autotuner picks between the two
+constexpr int min_blocks(int wpb) { return wpb >= 8 ? 2 : 6; }
+
 // ---------------------------------------------------------------------------
 // warp-level helpers
 
@@ -85,7 +90,7 @@ __device__ __forceinline__ void warp_range(unsigned G, unsigned w, unsigned nw, 
 // barriers: warps run independently.
 
 template <class K, int AMP, int KIND, int WPB, int IPT>
-__global__ void __launch_bounds__(WPB * 32, 20 / WPB)
+__global__ void __launch_bounds__(WPB * 32, min_blocks(WPB))
 k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, unsigned G) {
     typedef typename AmpT<AMP>::A A;
     typedef typename AmpT<AMP>::S S;
@@ -652,7 +657,7 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
 //     global scratch memory instead.  No block barriers.
 
 template <class K, int AMP, int KIND, int WPB>
-__global__ void __launch_bounds__(WPB * 32, 20 / WPB)
+__global__ void __launch_bounds__(WPB * 32, min_blocks(WPB))
 k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, unsigned G,
         unsigned SW, unsigned char* __restrict__ scratch, unsigned SS) {
     typedef typename AmpT<AMP>::ACC ACC;
