@@ -453,6 +453,7 @@ static void fill_desc(const fq_run* r, RunDesc& d, unsigned seg_base) {
     d.amp = r->amp;
     d.mode_det = r->det;
     d.theta = r->prm.threshold;
+    d.theta32 = (float)r->prm.threshold;
     d.t_rel = r->prm.t_rel;
     d.trel_one = r->prm.t_rel == 1.0;
     {

@@ -216,7 +216,11 @@ template <int KIND> struct RealModel {
     template <class K, class V>
     __device__ __forceinline__ static K offdiag(const ModelParams& p, K key, const Col& c, unsigned kk,
                                                 V& val) {
-        const int d = (int)(kk / (unsigned)c.n_occ), r = (int)(kk % (unsigned)c.n_occ);
+        // direction d = kk / n_occ < Z and rank r = kk mod n_occ, by comparisons
+        const unsigned no = (unsigned)c.n_occ;
+        int d = (int)(kk >= no);
+        if (Z == 4) d += (int)(kk >= 2u * no) + (int)(kk >= 3u * no);
+        const int r = (int)(kk - (unsigned)d * no);
         const int P = KeyOps<K>::nth(run_starts(key), r);
         if constexpr (KIND == FQ_KIND_REAL_1D) {
             // a hop to a neighbouring site only moves one separator: swap

@@ -84,10 +84,44 @@ __device__ __forceinline__ void warp_range(unsigned G, unsigned w, unsigned nw, 
 }
 
 // ---------------------------------------------------------------------------
+// asynchronous global -> shared copies (cp.async, 16-byte chunks; a chunk
+// with src_bytes < 16 reads only src_bytes and zero-fills the rest)
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, unsigned src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// a warp copies `bytes` from global (16-byte aligned) to shared
+__device__ __forceinline__ void warp_copy_async(void* dst, const void* src, unsigned bytes, int lane) {
+    for (unsigned o = (unsigned)lane * 16u; o < bytes; o += 32u * 16u)
+        cp_async16((unsigned char*)dst + o, (const unsigned char*)src + o,
+                   bytes - o < 16u ? bytes - o : 16u);
+}
+
+// ---------------------------------------------------------------------------
 // K1: spawning.  One warp per segment range; a segment is taken in batches
-// of up to 32 * IPT entries, each lane owning IPT consecutive entries, and
-// the batch's spawn indices are dealt round-robin to the lanes.  No block
-// barriers: warps run independently.
+// of up to 32 * IPT entries, staged in shared memory by cp.async one batch
+// ahead, each lane owning IPT consecutive entries; the batch's spawn
+// indices are dealt round-robin to the lanes.  A spawn's bucket slot is
+// reserved by an atomic whose result is used one round later, so the
+// atomics' latency overlaps the next round's work.  No block barriers.
+
+// dynamic shared memory of one spawn warp
+template <class K, int AMP, int CH> struct SpawnSmem {
+    typedef typename AmpT<AMP>::A A;
+    typedef typename AmpT<AMP>::C CO;
+    static constexpr size_t al(size_t b) { return (b + 15) / 16 * 16; }
+    static constexpr size_t key_off = 0;                                  // K [2][CH]
+    static constexpr size_t amp_off = key_off + al(2 * CH * sizeof(K));   // A [2][CH]
+    static constexpr size_t coef_off = amp_off + al(2 * CH * sizeof(A));  // CO [CH]
+    static constexpr size_t off_off = coef_off + al(CH * sizeof(CO));     // unsigned [CH + 1]
+    static constexpr size_t m_off = off_off + al((CH + 1) * sizeof(unsigned));  // unsigned [CH]
+    static constexpr size_t bytes = m_off + al(CH * sizeof(unsigned));
+};
 
 template <class K, int AMP, int KIND, int WPB, int IPT>
 __global__ void __launch_bounds__(WPB * 32, min_blocks(WPB))
@@ -97,209 +131,58 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     typedef typename AmpT<AMP>::C CO;
     typedef Model<KIND> MD;
     typedef typename MD::Col Col;
+    typedef SpawnSmem<K, AMP, 32 * IPT> SM;
     constexpr int CH = 32 * IPT;
-    __shared__ K s_key[WPB][CH];
-    __shared__ CO s_coef[WPB][CH];
-    __shared__ unsigned s_off[WPB][CH + 1];
-    __shared__ unsigned s_m[WPB][CH];
+    constexpr int U = 2;  // spawns per lane per round
+    extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    K* const wkey = s_key[wib];
-    CO* const wcoef = s_coef[wib];
-    unsigned* const woff = s_off[wib];
-    unsigned* const wm = s_m[wib];
+    unsigned char* const wbase = smem + (size_t)wib * SM::bytes;
+    K* const in_key = (K*)(wbase + SM::key_off);
+    A* const in_amp = (A*)(wbase + SM::amp_off);
+    CO* const wcoef = (CO*)(wbase + SM::coef_off);
+    unsigned* const woff = (unsigned*)(wbase + SM::off_off);
+    unsigned* const wm = (unsigned*)(wbase + SM::m_off);
     unsigned g0, g1;
     warp_range(G, blockIdx.x * WPB + wib, gridDim.x * WPB, g0, g1);
 
+    // the run of the current item and its per-step constants
     const RunDesc* R = nullptr;
     int cur_r = -1;
-    unsigned err = 0, cur = 0;
+    unsigned err = 0;
+    const K* vk0 = nullptr;
+    const A* va0 = nullptr;
+    const unsigned* vcnt = nullptr;
+    unsigned Cv = 0, Cs = 0, seg_base = 0, stepno = 0;
+    K* sk = nullptr;
+    S* sv = nullptr;
+    unsigned* sfill = nullptr;
+    int log2B = 0;
+    double dt = 0.0;
+    uint2 rkey = make_uint2(0, 0);
     unsigned long long n_ex = 0, n_inex = 0, n_sp = 0;
 
-    for (unsigned g = g0; g < g1; ++g) {
-        const int r = (int)seg_run[g];
-        if (r != cur_r) {  // warp-uniform
-            if (R) {
-                n_ex = warp_sum(n_ex);
-                n_inex = warp_sum(n_inex);
-                n_sp = warp_sum(n_sp);
-                if (lane == 0) {
-                    if (n_ex) atomicAdd(&R->st->n_exact, n_ex);
-                    if (n_inex) atomicAdd(&R->st->n_inexact, n_inex);
-                    if (n_sp) atomicAdd(&R->st->n_spawns, n_sp);
-                }
-                n_ex = n_inex = n_sp = 0;
+    // spawns whose bucket slot is being reserved (stored one round later)
+    K pd[U];
+    S pv[U];
+    unsigned pb[U], pp[U];
+    bool ph[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) ph[u] = false;
+
+    auto flush_pending = [&]() {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!ph[u]) continue;
+            if (pp[u] < Cs) {
+                sk[(size_t)pb[u] * Cs + pp[u]] = pd[u];
+                sv[(size_t)pb[u] * Cs + pp[u]] = pv[u];
+            } else {
+                atomicOr(&R->st->err, FQ_DERR_SPAWN_CAP);
             }
-            R = runs + r;
-            cur_r = r;
-            // lane 0 reads, the warp shares: another warp may set an error bit
-            unsigned e = 0, c = 0;
-            if (lane == 0) {
-                e = *(volatile unsigned*)&R->st->err;
-                c = (unsigned)R->st->cur;
-            }
-            err = __shfl_sync(0xFFFFFFFFu, e, 0);
-            cur = __shfl_sync(0xFFFFFFFFu, c, 0);
+            ph[u] = false;
         }
-        if (err) continue;
-        const unsigned seg = g - R->seg_base;
-        const unsigned n = R->vcount[cur][seg];
-        if (n == 0) continue;
-
-        const ModelParams& mp = R->mp;
-        const K* __restrict__ vk = (const K*)R->vkeys[cur] + (size_t)seg * R->Cv;
-        const A* __restrict__ va = (const A*)R->vamps[cur] + (size_t)seg * R->Cv;
-        K* __restrict__ sk = (K*)R->skeys;
-        S* __restrict__ sv = (S*)R->samps;
-        unsigned* __restrict__ sfill = R->sfill;
-        const unsigned Cs = R->Cs;
-        const int log2B = R->log2B;
-        const double dt = R->st->dt;
-        const int det = R->mode_det, trel_one = R->trel_one;
-        const double t_rel = R->t_rel;
-        const int mmax = R->mmax;
-        const unsigned stepno = (unsigned)(R->st->step + 1);
-        const uint2 rkey = make_uint2(R->key_x, R->key_y);
-
-        for (unsigned c0 = 0; c0 < n; c0 += CH) {
-            const unsigned cn = min((unsigned)CH, n - c0);
-            // stage keys and amplitudes (coalesced); the amplitudes go through
-            // the coefficient slots and are overwritten below
-#pragma unroll
-            for (int j = 0; j < IPT; ++j) {
-                const unsigned i = j * 32 + lane;
-                if (i < cn) {
-                    wkey[i] = vk[c0 + i];
-                    wcoef[i] = (CO)va[c0 + i];
-                }
-            }
-            __syncwarp();
-            unsigned cnt[IPT], tsum = 0;
-            CO coef[IPT];
-#pragma unroll
-            for (int j = 0; j < IPT; ++j) {
-                const unsigned i = lane * IPT + j;
-                unsigned c_i = 0;
-                coef[j] = (CO)0;
-                if (i < cn) {
-                    const K key = wkey[i];
-                    const CO c = wcoef[i];
-                    Col col;
-                    const unsigned m = MD::num_offdiag(mp, key, col);
-                    unsigned fl, ce;
-                    floor_ceil_abs(c, fl, ce);
-                    if (AMP == FQ_AMP_INT) {
-                        // integer walkers: |c| attempts, never an exact column;
-                        // the coefficient is dt m (spawn probability per |H_ji|)
-                        c_i = m ? fl : 0u;
-                        ++n_inex;
-                        coef[j] = (CO)(dt * (double)m);
-                        wm[i] = m | (c < (CO)0 ? 0x40000000u : 0u);
-                    } else {
-                        bool ex;
-                        if (det) ex = true;
-                        else if (trel_one) ex = fl >= m;  // |c| >= m for an integer m
-                        else ex = fabs((double)c) * t_rel >= (double)m;
-                        c_i = ex ? m : ce;
-                        if (ex) {
-                            ++n_ex;
-                            coef[j] = (-(CO)dt) * c;
-                        } else {
-                            ++n_inex;
-                            CO ratio;
-                            if (KIND != FQ_KIND_MOM_1D && (int)m <= mmax && (int)ce <= mmax) {
-                                const size_t ri = (size_t)m * (size_t)(mmax + 1) + ce;
-                                if constexpr (AMP == FQ_AMP_F32) ratio = __ldg(R->ratio32 + ri);
-                                else ratio = __ldg(R->ratio64 + ri);
-                            } else {
-                                ratio = (CO)m / (CO)ce;
-                            }
-                            coef[j] = ((-(CO)dt) * ratio) * c;
-                        }
-                        wm[i] = m | (ex ? 0x80000000u : 0u);
-                    }
-                }
-                cnt[j] = c_i;
-                tsum += c_i;
-            }
-            const unsigned incl = warp_incl_scan(tsum, lane);
-            const unsigned total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-            unsigned off = incl - tsum;
-#pragma unroll
-            for (int j = 0; j < IPT; ++j) {
-                woff[lane * IPT + j] = off;
-                wcoef[lane * IPT + j] = coef[j];
-                off += cnt[j];
-            }
-            if (lane == 31) woff[CH] = total;
-            __syncwarp();
-
-            // U spawns per lane per round: all their slot reservations are in
-            // flight together before any store waits on one
-            constexpr int U = 2;
-            for (unsigned q0 = 0; q0 < total; q0 += 32 * U) {
-                K dest[U];
-                S val[U];
-                unsigned bk[U], pos[U];
-                bool has[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const unsigned q = q0 + u * 32 + lane;
-                    has[u] = false;
-                    if (q >= total) continue;
-                    int i = 0;
-#pragma unroll
-                    for (int step = CH / 2; step >= 1; step >>= 1)
-                        if (woff[i + step] <= q) i += step;
-                    const unsigned a = q - woff[i];
-                    const K key = wkey[i];
-                    const CO cf = wcoef[i];
-                    const unsigned mm = wm[i];
-                    const unsigned m = mm & 0x3FFFFFFFu;
-                    const bool ex = (AMP != FQ_AMP_INT) && (mm >> 31);
-                    Col col;
-                    MD::num_offdiag(mp, key, col);
-                    uint4 w = make_uint4(0, 0, 0, 0);
-                    unsigned kk = a;
-                    if (!ex) {
-                        w = draw(rkey, stepno, a, KeyOps<K>::rng_h(key));
-                        kk = pick(w, m);
-                    }
-                    if constexpr (AMP == FQ_AMP_INT) {
-                        double hv;
-                        dest[u] = MD::offdiag(mp, key, col, kk, hv);
-                        const double p = fabs(hv) * cf;
-                        const double fl = floor(p);
-                        const long long nw = (long long)fl + (uniform53(w) < p - fl ? 1 : 0);
-                        if (!nw) continue;
-                        const int sg = (hv > 0.0 ? -1 : 1) * ((mm & 0x40000000u) ? -1 : 1);
-                        val[u] = (S)(sg * nw);
-                    } else {
-                        CO hv;
-                        dest[u] = MD::offdiag(mp, key, col, kk, hv);
-                        val[u] = hv * cf;
-                    }
-                    has[u] = true;
-                    bk[u] = segment_of(fmix64(KeyOps<K>::rng_h(dest[u])), log2B);
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if (has[u]) pos[u] = atomicAdd(&sfill[bk[u]], 1u);
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    if (!has[u]) continue;
-                    ++n_sp;
-                    if (pos[u] < Cs) {
-                        sk[(size_t)bk[u] * Cs + pos[u]] = dest[u];
-                        sv[(size_t)bk[u] * Cs + pos[u]] = val[u];
-                    } else {
-                        atomicOr(&R->st->err, FQ_DERR_SPAWN_CAP);
-                    }
-                }
-            }
-            __syncwarp();
-        }
-    }
-    if (R) {
+    };
+    auto flush_counts = [&]() {
         n_ex = warp_sum(n_ex);
         n_inex = warp_sum(n_inex);
         n_sp = warp_sum(n_sp);
@@ -308,17 +191,228 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
             if (n_inex) atomicAdd(&R->st->n_inexact, n_inex);
             if (n_sp) atomicAdd(&R->st->n_spawns, n_sp);
         }
+        n_ex = n_inex = n_sp = 0;
+    };
+    // make run r current (warp-uniform)
+    auto enter_run = [&](int r) {
+        if (R) {
+            flush_pending();
+            flush_counts();
+        }
+        R = runs + r;
+        cur_r = r;
+        // lane 0 reads, the warp shares: another warp may set an error bit
+        unsigned e = 0, c = 0;
+        if (lane == 0) {
+            e = *(volatile unsigned*)&R->st->err;
+            c = (unsigned)R->st->cur;
+        }
+        err = __shfl_sync(0xFFFFFFFFu, e, 0);
+        const unsigned cur = __shfl_sync(0xFFFFFFFFu, c, 0);
+        vk0 = (const K*)R->vkeys[cur];
+        va0 = (const A*)R->vamps[cur];
+        vcnt = R->vcount[cur];
+        Cv = R->Cv;
+        Cs = R->Cs;
+        seg_base = R->seg_base;
+        sk = (K*)R->skeys;
+        sv = (S*)R->samps;
+        sfill = R->sfill;
+        log2B = R->log2B;
+        dt = R->st->dt;
+        stepno = (unsigned)(R->st->step + 1);
+        rkey = make_uint2(R->key_x, R->key_y);
+    };
+    // the next non-empty segment of the current run at or after g (g1 if none
+    // before the run changes or the range ends); n = its entry count
+    auto next_segment = [&](unsigned g, unsigned& n) -> unsigned {
+        for (; g < g1; ++g) {
+            if ((int)seg_run[g] != cur_r) return g;  // run change: handled by the caller
+            if (err) continue;
+            n = vcnt[g - seg_base];
+            if (n) return g;
+        }
+        return g1;
+    };
+    auto stage = [&](unsigned g, unsigned c0, unsigned cn, int b) {
+        const size_t e0 = (size_t)(g - seg_base) * Cv + c0;
+        warp_copy_async(in_key + b * CH, vk0 + e0, cn * (unsigned)sizeof(K), lane);
+        warp_copy_async(in_amp + b * CH, va0 + e0, cn * (unsigned)sizeof(A), lane);
+        cp_async_commit();
+    };
+
+    // current item (segment g, entries [c0, c0 + CH) of n), staged in buffer b
+    unsigned g = g0, c0 = 0, n = 0;
+    int b = 0;
+    bool staged = false;
+    while (true) {
+        if (g < g1 && (int)seg_run[g] != cur_r) {
+            enter_run((int)seg_run[g]);
+            staged = false;
+        }
+        if (!staged) {
+            g = next_segment(g, n);
+            if (g >= g1) break;
+            if ((int)seg_run[g] != cur_r) continue;
+            c0 = 0;
+            stage(g, 0, min((unsigned)CH, n), b);
+        }
+        const unsigned cn = min((unsigned)CH, n - c0);
+        cp_async_wait_all();
+        __syncwarp();
+        // stage the next item of the same run into the other buffer
+        unsigned ng = g, nc0 = c0 + CH, nn = n;
+        if (nc0 >= n) {
+            nc0 = 0;
+            ng = next_segment(g + 1, nn);
+        }
+        staged = ng < g1 && (int)seg_run[ng] == cur_r;
+        if (staged) stage(ng, nc0, min((unsigned)CH, nn - nc0), b ^ 1);
+
+        const K* wkey = in_key + b * CH;
+        const A* wamp = in_amp + b * CH;
+        const ModelParams& mp = R->mp;
+        unsigned cnt[IPT], tsum = 0;
+        CO coef[IPT];
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            const unsigned i = lane * IPT + j;
+            unsigned c_i = 0;
+            coef[j] = (CO)0;
+            if (i < cn) {
+                const K key = wkey[i];
+                const CO c = (CO)wamp[i];
+                Col col;
+                const unsigned m = MD::num_offdiag(mp, key, col);
+                unsigned fl, ce;
+                floor_ceil_abs(c, fl, ce);
+                if (AMP == FQ_AMP_INT) {
+                    // integer walkers: |c| attempts, never an exact column;
+                    // the coefficient is dt m (spawn probability per |H_ji|)
+                    c_i = m ? fl : 0u;
+                    ++n_inex;
+                    coef[j] = (CO)(dt * (double)m);
+                    wm[i] = m | (c < (CO)0 ? 0x40000000u : 0u);
+                } else {
+                    bool ex;
+                    if (R->mode_det) ex = true;
+                    else if (R->trel_one) ex = fl >= m;  // |c| >= m for an integer m
+                    else ex = fabs((double)c) * R->t_rel >= (double)m;
+                    c_i = ex ? m : ce;
+                    if (ex) {
+                        ++n_ex;
+                        coef[j] = (-(CO)dt) * c;
+                    } else {
+                        ++n_inex;
+                        CO ratio;
+                        const int mmax = R->mmax;
+                        if (KIND != FQ_KIND_MOM_1D && (int)m <= mmax && (int)ce <= mmax) {
+                            const size_t ri = (size_t)m * (size_t)(mmax + 1) + ce;
+                            if constexpr (AMP == FQ_AMP_F32) ratio = __ldg(R->ratio32 + ri);
+                            else ratio = __ldg(R->ratio64 + ri);
+                        } else {
+                            ratio = (CO)m / (CO)ce;
+                        }
+                        coef[j] = ((-(CO)dt) * ratio) * c;
+                    }
+                    wm[i] = m | (ex ? 0x80000000u : 0u);
+                }
+            }
+            cnt[j] = c_i;
+            tsum += c_i;
+        }
+        const unsigned incl = warp_incl_scan(tsum, lane);
+        const unsigned total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        unsigned off = incl - tsum;
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            woff[lane * IPT + j] = off;
+            wcoef[lane * IPT + j] = coef[j];
+            off += cnt[j];
+        }
+        if (lane == 31) woff[CH] = total;
+        __syncwarp();
+
+        for (unsigned q0 = 0; q0 < total; q0 += 32 * U) {
+            K dest[U];
+            S val[U];
+            unsigned bk[U];
+            bool has[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const unsigned q = q0 + u * 32 + lane;
+                has[u] = false;
+                if (q >= total) continue;
+                int i = 0;
+#pragma unroll
+                for (int st = CH / 2; st >= 1; st >>= 1)
+                    if (woff[i + st] <= q) i += st;
+                const unsigned a = q - woff[i];
+                const K key = wkey[i];
+                const CO cf = wcoef[i];
+                const unsigned mm = wm[i];
+                const unsigned m = mm & 0x3FFFFFFFu;
+                const bool ex = (AMP != FQ_AMP_INT) && (mm >> 31);
+                Col col;
+                if constexpr (KIND != FQ_KIND_MOM_1D) col.n_occ = (int)(m / (unsigned)MD::Z);
+                else MD::num_offdiag(mp, key, col);
+                uint4 w = make_uint4(0, 0, 0, 0);
+                unsigned kk = a;
+                if (!ex) {
+                    w = draw(rkey, stepno, a, KeyOps<K>::rng_h(key));
+                    kk = pick(w, m);
+                }
+                if constexpr (AMP == FQ_AMP_INT) {
+                    double hv;
+                    dest[u] = MD::offdiag(mp, key, col, kk, hv);
+                    const double p = fabs(hv) * cf;
+                    const double fl = floor(p);
+                    const long long nw = (long long)fl + (uniform53(w) < p - fl ? 1 : 0);
+                    if (!nw) continue;
+                    const int sg = (hv > 0.0 ? -1 : 1) * ((mm & 0x40000000u) ? -1 : 1);
+                    val[u] = (S)(sg * nw);
+                } else {
+                    CO hv;
+                    dest[u] = MD::offdiag(mp, key, col, kk, hv);
+                    val[u] = hv * cf;
+                }
+                has[u] = true;
+                bk[u] = segment_of(fmix64(KeyOps<K>::rng_h(dest[u])), log2B);
+            }
+            unsigned pos[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (has[u]) pos[u] = atomicAdd(&sfill[bk[u]], 1u);
+            flush_pending();  // the previous round's slots have arrived by now
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (!has[u]) continue;
+                ++n_sp;
+                pd[u] = dest[u];
+                pv[u] = val[u];
+                pb[u] = bk[u];
+                pp[u] = pos[u];
+                ph[u] = true;
+            }
+        }
+        __syncwarp();  // every lane is done with buffer b
+        if (!staged) {
+            g = ng;
+            continue;
+        }
+        g = ng;
+        c0 = nc0;
+        n = nn;
+        b ^= 1;
+    }
+    if (R) {
+        flush_pending();
+        flush_counts();
     }
 }
 
 // ---------------------------------------------------------------------------
 // on-chip open-addressing table (linear probing, CAS on the key)
-
-__device__ __forceinline__ void acc_add(double* p, double v) { atomicAdd(p, v); }
-__device__ __forceinline__ void acc_add(float* p, float v) { atomicAdd(p, v); }
-__device__ __forceinline__ void acc_add(long long* p, long long v) {
-    atomicAdd((unsigned long long*)p, (unsigned long long)v);
-}
 
 __device__ __forceinline__ uint64_t key_cas(uint64_t* p, uint64_t cmp, uint64_t val) {
     return (uint64_t)atomicCAS((unsigned long long*)p, (unsigned long long)cmp,
@@ -394,7 +488,11 @@ __device__ __forceinline__ bool compress(typename AmpT<AMP>::ACC w, const RunDes
             const uint4 r = draw(rkey, stepno, 0xFFFFFFFFu, h);
             if (!(uniform53(r) < aw / theta)) return false;
         }
-        out = w < (ACC)0 ? (ACC)(-theta) : (ACC)theta;
+        // sign(w) theta, on the bits
+        if constexpr (AMP == FQ_AMP_F64)
+            out = bdouble(dbits(theta) | (dbits(w) & 0x8000000000000000ull));
+        else
+            out = __uint_as_float(__float_as_uint(R->theta32) | (__float_as_uint(w) & 0x80000000u));
         return true;
     }
 }
@@ -536,7 +634,16 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
             if (j < n_sp) {
                 q = table_insert(tk, mask, key, nw);
                 if (q < 0) acc.full = true;
-                else acc_add(&ta[q], (ACC)v);
+            }
+            // the table is the warp's own: only lanes of this round that hit
+            // the same slot conflict.  They pass their values to the lowest
+            // of them, which adds the group's sum with a plain update.
+            const unsigned grp = __match_any_sync(0xFFFFFFFFu, q);
+            if (q >= 0) {
+                ACC sum = (ACC)v;
+                for (unsigned o = grp & (grp - 1u); o; o &= o - 1u)
+                    sum = sum + (ACC)__shfl_sync(grp, v, __ffs(o) - 1);
+                if (lane == __ffs(grp) - 1) ta[q] = ta[q] + sum;
             }
             const unsigned bal = __ballot_sync(0xFFFFFFFFu, nw);
             if (nw) tl[nl + __popc(bal & ((1u << lane) - 1u))] = (unsigned)q;

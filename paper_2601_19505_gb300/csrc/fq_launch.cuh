@@ -12,12 +12,15 @@ template <class K, int AMP, int KIND> struct Launch {
     typedef typename AmpT<AMP>::S S;
     typedef typename AmpT<AMP>::ACC ACC;
 
+    static constexpr size_t spawn_smem(int wpb) {
+        return (size_t)wpb * SpawnSmem<K, AMP, 128>::bytes;
+    }
     static void spawn(const LaunchCfg& c, const RunDesc* d, const unsigned* sr, unsigned G,
                       cudaStream_t s) {
         if (c.spawn_wpb == 4)
-            k_spawn<K, AMP, KIND, 4, 4><<<c.spawn_grid, 128, 0, s>>>(d, sr, G);
+            k_spawn<K, AMP, KIND, 4, 4><<<c.spawn_grid, 128, spawn_smem(4), s>>>(d, sr, G);
         else
-            k_spawn<K, AMP, KIND, 8, 4><<<c.spawn_grid, 256, 0, s>>>(d, sr, G);
+            k_spawn<K, AMP, KIND, 8, 4><<<c.spawn_grid, 256, spawn_smem(8), s>>>(d, sr, G);
     }
     static void merge(const LaunchCfg& c, const RunDesc* d, const unsigned* sr, unsigned G,
                       cudaStream_t s) {
@@ -32,16 +35,25 @@ template <class K, int AMP, int KIND> struct Launch {
     static cudaError_t prepare(size_t smem) {
         cudaError_t e = cudaFuncSetAttribute(k_merge<K, AMP, KIND, 4>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        return cudaFuncSetAttribute(k_merge<K, AMP, KIND, 8>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_merge<K, AMP, KIND, 8>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_spawn<K, AMP, KIND, 4, 4>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spawn_smem(4));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_spawn<K, AMP, KIND, 8, 4>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spawn_smem(8));
+        return e;
     }
     static int spawn_occupancy(int wpb) {
         int n = 0;
         if (wpb == 4)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spawn<K, AMP, KIND, 4, 4>, 128, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spawn<K, AMP, KIND, 4, 4>, 128,
+                                                          spawn_smem(4));
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spawn<K, AMP, KIND, 8, 4>, 256, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spawn<K, AMP, KIND, 8, 4>, 256,
+                                                          spawn_smem(8));
         return n;
     }
     static int merge_occupancy(int wpb, size_t smem) {

@@ -74,6 +74,7 @@ struct RunDesc {
     int amp;            // FQ_AMP_*
     int mode_det;       // deterministic limit: every column exact, no compression
     double theta, t_rel;
+    float theta32;      // (float)theta
     int theta_pow2;     // theta = 2^theta_exp: compression decided in integers
     int theta_exp;
     int norm_q;         // exact norm unit 2^norm_q
