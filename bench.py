@@ -28,6 +28,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -318,8 +319,9 @@ def gpu_arm(args, cfg, name):
         done += k
     tune_steps = 0
     if not args.no_autotune:
+        s_before = run.stats()["step"]
         run.autotune(2)
-        tune_steps = 3 * 8
+        tune_steps = run.stats()["step"] - s_before
     run.step(args.warmup)
     run.stats()
     run.history()  # drain
@@ -394,7 +396,8 @@ def gpu_arm(args, cfg, name):
                        "autotune_steps": tune_steps, "len_mean": L_mean,
                        "spawns_mean": S_mean, "graph_replay": True,
                        "l2": "working set per step %.2f GB > 129 MB L2; no flush" % (ws / 1e9),
-                       "parallelism": "replicas x%d" % world},
+                       "parallelism": "replicas x%d" % world,
+                       "launch_shape": run.shape()},
             "roofline": {"bound": "hbm", "kernel": "k_" + dom, "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
@@ -415,6 +418,128 @@ def gpu_arm(args, cfg, name):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Equal-error comparison: the 64 runs of c4 stepped as one FP32 batch against
+# the same 64 runs stepped one after another in plain FP64
+
+def equal_error_arm(args):
+    import torch
+
+    import paper_2601_19505_gb300 as fq
+    from paper_2601_19505_gb300 import analysis as A
+
+    torch.cuda.set_device(0)
+    cfgs = W.batch_configs(64, seed=1)
+    steps = cfgs[0]["steps"]
+    equil = steps // 4
+    timed = steps - equil
+
+    def make(c, mode):
+        h = fq.Hamiltonian(c["kind"], c["Lx"], c["Ly"], c["N"], c["t"], c["u"])
+        p = fq.default_params(mode=MODE_CODE[mode], dt=c["dt"], target=c["target"],
+                              seed=c["seed"], run_id=c["run_id"])
+        r = fq.Run(h, p)
+        r.seed_default(W.START_WEIGHT)
+        return h, r
+
+    def timed_steps(step_fn, stream_handle, n):
+        stream = torch.cuda.ExternalStream(stream_handle) if stream_handle \
+            else torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        step_fn(n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    def estimates(hist):
+        e = A.ratio_estimate(hist["hproj"], hist["vproj"])
+        sh = A.blocked_mean(hist["shift"])
+        return (e["ratio"], e["err"], float(hist["len"].sum()), sh["mean"], sh["err"],
+                float(np.mean(hist["vproj"])), float(np.mean(hist["len"])))
+
+    # FP32 amplitudes, all 64 runs in one launch per kernel per step
+    made = [make(c, "REAL32") for c in cfgs]
+    runs32 = [r for _, r in made]
+    batch = fq.Batch(runs32)
+    batch.step(equil)
+    try:
+        batch.sync()
+    except fq.FqError:
+        bad = [(c["run_id"], c["Lx"], c["target"], r.error_bits(), r.capacity())
+               for c, r in zip(cfgs, runs32) if r.error_bits()]
+        raise RuntimeError("batched FP32 runs failed: %s" % bad)
+    tune = 0
+    if not args.no_autotune:
+        batch.autotune(2)
+        tune = 1
+    batch.sync()
+    for r in runs32:
+        r.history()
+    t32 = timed_steps(batch.step, runs32[0].stream, timed)
+    if batch.sync():
+        raise RuntimeError("batched FP32 runs failed")
+    est32 = [estimates(r.history()) for r in runs32]
+    batch.close()
+    for r in runs32:
+        r.close()
+
+    # plain FP64, one run after another
+    t64, est64 = 0.0, []
+    for c in cfgs:
+        h, r = make(c, "REAL64")
+        r.step(equil)
+        r.sync()
+        r.history()
+        t64 += timed_steps(r.step, r.stream, timed)
+        if r.sync():
+            raise RuntimeError("FP64 run %d failed" % c["run_id"])
+        est64.append(estimates(r.history()))
+        r.close()
+
+    u32 = sum(e[2] for e in est32)
+    u64 = sum(e[2] for e in est64)
+    # the projected energy where both forms give a finite estimate with an
+    # error bar, else the shift estimator
+    use = []
+    for a, b in zip(est32, est64):
+        fin = all(np.isfinite(v) and v != 0.0 for v in (a[0], a[1], b[0], b[1]))
+        use.append((a[0], a[1], b[0], b[1], "projected") if fin else (a[3], a[4], b[3], b[4], "shift"))
+    var_ratio = np.array([(u[1] / u[3]) ** 2 for u in use])
+    agree = sum(1 for u in use if abs(u[0] - u[2]) <= 2.0 * math.hypot(u[1], u[3]))
+    # time for every run to reach the FP64 runs' error bars: the batch runs
+    # until its worst (or median) run's variance matches
+    speed_med = t64 / (t32 * float(np.median(var_ratio)))
+    speed_worst = t64 / (t32 * float(var_ratio.max()))
+    line = {"metric": METRIC + " (batched FP32 vs sequential FP64 at equal error)",
+            "value": u32 / t32, "unit": UNIT, "n_gpus": 1, "steps": timed, "warmup": equil,
+            "ms_per_step": 1e3 * t32 / timed, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "c4: 64 periodic 1D real-space Bose-Hubbard runs, M = N ~ "
+                                   "U{10..30}, U/t ~ U[1, 10], N_t log-uniform in [1e4, 1e6] "
+                                   "(default_rng(1)), dt = 1e-3, 5000 steps (first 25 % "
+                                   "untimed), 10 walkers on uniform filling",
+                       "autotuned": bool(tune)},
+            "equal_error": {
+                "fp32_batch": {"seconds": t32, "configs_per_s": u32 / t32},
+                "fp64_sequential": {"seconds": t64, "configs_per_s": u64 / t64},
+                "runs": len(cfgs),
+                "energies_agree_2sigma": agree,
+                "median_var_ratio_fp32_over_fp64": float(np.median(var_ratio)),
+                "max_var_ratio_fp32_over_fp64": float(var_ratio.max()),
+                "speedup_to_equal_error_median": speed_med,
+                "speedup_to_equal_error_worst": speed_worst,
+                "estimator_shift_runs": sum(1 for u in use if u[4] == "shift"),
+                "median_err_fp64": float(np.median([u[3] for u in use])),
+                "per_run": [{"M": c["Lx"], "U": round(c["u"], 4), "N_t": round(c["target"]),
+                             "E32": u[0], "err32": u[1], "E64": u[2], "err64": u[3], "est": u[4],
+                             "S32": a[3], "S64": b[3], "vproj64": b[5], "len64": b[6]}
+                            for c, u, a, b in zip(cfgs, use, est32, est64)]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -425,6 +550,9 @@ def main():
     ap.add_argument("--equil", type=int, default=None)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--equal-error", action="store_true",
+                    help="the c4 comparison: 64 runs as one FP32 batch against the same runs "
+                         "one after another in FP64, at equal projected-energy error")
     ap.add_argument("--mode", choices=sorted(MODE_CODE), default=None,
                     help="override the workload's amplitude mode (exploration only)")
     args = ap.parse_args()
@@ -435,6 +563,8 @@ def main():
         cfg["mode"] = args.mode
     if args.impl == "reference":
         return reference_arm(args, cfg, args.config)
+    if args.equal_error:
+        return equal_error_arm(args)
     return gpu_arm(args, cfg, args.config)
 
 

@@ -228,6 +228,11 @@ int fq_run_capacity(const fq_run *r, size_t *capacity_vec, size_t *capacity_spaw
 /* Time the launch shapes on the current vector and keep the fastest.  Each
  * candidate runs `steps` real steps, so the run advances. */
 int fq_run_autotune(fq_run *r, int steps);
+/* The launch shape the run steps with (after fq_run_autotune, the tuned
+ * one): shape[0..5] = spawn warps per block, spawn blocks, merge warps per
+ * block, merge blocks, on-chip table slots per merge warp, scratch table
+ * slots per merge warp.  Needs a seeded run. */
+int fq_run_shape(fq_run *r, int *shape);
 /* Measurement: run n steps launched one kernel at a time (not from the graph)
  * with CUDA events around each kernel on the run's stream; ms[0], ms[1],
  * ms[2] = mean milliseconds per step of the spawning, merge and shift

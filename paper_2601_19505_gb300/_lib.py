@@ -76,6 +76,7 @@ SYMBOLS = {
     "fq_run_autotune": (C.c_int, [C.c_void_p, C.c_int]),
     "fq_run_reserve": (C.c_int, [C.c_void_p, C.c_size_t, C.c_size_t]),
     "fq_run_capacity": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+    "fq_run_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "fq_run_profile": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_float)]),
     "fq_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int]),
     "fq_batch_destroy": (None, [C.c_void_p]),

@@ -576,11 +576,14 @@ extern "C" int fq_run_create(fq_run** out, const fq_ham* h, const fq_params* p, 
     double dim = 0;
     fq_ham_dimension(h, &dim);
     const double th = r->det ? 1.0 : (p->mode == FQ_MODE_INT ? 1.0 : std::min(1.0, p->threshold));
-    double lcap = p->capacity_vec ? (double)p->capacity_vec : 2.0 * p->target / th + 1024.0;
+    // the spawn count follows the norm, not the occupied count: when the
+    // vector fills a small Hilbert space its entries grow and spawn more
+    const double lnorm = p->capacity_vec ? (double)p->capacity_vec : 2.0 * p->target / th + 1024.0;
+    double lcap = lnorm;
     if (r->det && !p->capacity_vec) lcap = std::min(dim * 1.05 + 1024.0, 1.0e9);
     lcap = std::min(lcap, dim * 1.05 + 1024.0);
     double scap = p->capacity_spawn ? (double)p->capacity_spawn
-                                    : 1.5 * lcap * std::max(1.0, p->t_rel) + 4096.0;
+                                    : 1.5 * lnorm * std::max(1.0, p->t_rel) + 4096.0;
     if (r->det && !p->capacity_spawn) scap = lcap * (double)max_offdiag(h->mp) + 4096.0;
     if (lcap > 4.0e9 || scap > 8.0e9) {
         delete r;
@@ -591,7 +594,7 @@ extern "C" int fq_run_create(fq_run** out, const fq_ham* h, const fq_params* p, 
     // spawns ~ len) the spawns into a bucket fill about a third of one merge
     // warp's on-chip table (the table holds spawned addresses only)
     r->slots = warp_slots(r->ks);
-    double l_ss = std::min(p->target / th, dim), s_ss = 1.1 * l_ss;
+    double l_ss = std::min(p->target / th, dim), s_ss = 1.1 * p->target / th;
     if (r->det) {
         l_ss = std::min(lcap, dim);
         s_ss = l_ss * (double)max_offdiag(h->mp);
@@ -1426,28 +1429,65 @@ extern "C" int fq_run_spawns(fq_run* r, fq_key* dest, double* val, size_t cap, s
 
 static int autotune(fq_batch* b, int steps) {
     if (steps < 1) return FQ_ERR_INVALID;
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    float best = 1e30f;
-    LaunchCfg bestc = b->cfg;
-    for (size_t i = 1; i < b->shapes.size(); ++i) {
-        b->cfg = b->shapes[i];
-        enqueue_steps(b, 1, b->stream);  // warm
-        cudaEventRecord(e0, b->stream);
-        enqueue_steps(b, steps, b->stream);
-        cudaEventRecord(e1, b->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) break;
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-            best = ms;
-            bestc = b->cfg;
-        }
+    // the spawn and merge kernels are independent launches: their shapes are
+    // timed separately (CUDA events around each kernel) and chosen separately
+    std::vector<LaunchCfg> sc, mc;
+    for (const LaunchCfg& c : b->shapes) {
+        bool seen_s = false, seen_m = false;
+        for (const LaunchCfg& x : sc) seen_s |= x.spawn_wpb == c.spawn_wpb && x.spawn_grid == c.spawn_grid;
+        for (const LaunchCfg& x : mc)
+            seen_m |= x.merge_wpb == c.merge_wpb && x.merge_grid == c.merge_grid && x.slots == c.slots;
+        if (!seen_s) sc.push_back(c);
+        if (!seen_m) mc.push_back(c);
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    b->cfg = bestc;
+    const size_t nc = std::max(sc.size(), mc.size());
+    const size_t total = nc * (size_t)steps;
+    std::vector<cudaEvent_t> ev(3 * total, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < ev.size() && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+    const int nr = (int)b->runs.size();
+    auto shape = [&](size_t i) {
+        LaunchCfg c = mc[i % mc.size()];
+        const LaunchCfg& s2 = sc[i % sc.size()];
+        c.spawn_wpb = s2.spawn_wpb;
+        c.spawn_grid = s2.spawn_grid;
+        return c;
+    };
+    if (e == cudaSuccess) enqueue_steps(b, 1, b->stream);  // warm
+    for (size_t t = 0; t < total && e == cudaSuccess; ++t) {
+        const LaunchCfg c = shape(t % nc);
+        cudaEventRecord(ev[3 * t], b->stream);
+        b->ks->spawn(c, b->d_desc, b->d_seg_run, b->G, b->stream);
+        cudaEventRecord(ev[3 * t + 1], b->stream);
+        b->ks->merge(c, b->d_desc, b->d_seg_run, b->G, b->stream);
+        e = cudaEventRecord(ev[3 * t + 2], b->stream);
+        launch_shift(b->d_desc, nr, b->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    std::vector<double> ts(sc.size(), 0.0), tm(mc.size(), 0.0);
+    std::vector<int> ns(sc.size(), 0), nm(mc.size(), 0);
+    for (size_t t = 0; t < total && e == cudaSuccess; ++t) {
+        float a = 0, m = 0;
+        e = cudaEventElapsedTime(&a, ev[3 * t], ev[3 * t + 1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&m, ev[3 * t + 1], ev[3 * t + 2]);
+        const size_t i = t % nc;
+        ts[i % sc.size()] += a;
+        ns[i % sc.size()] += 1;
+        tm[i % mc.size()] += m;
+        nm[i % mc.size()] += 1;
+    }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    if (e != cudaSuccess) return cuda_err(e);
+    size_t bs = 0, bm = 0;
+    for (size_t i = 1; i < sc.size(); ++i)
+        if (ts[i] / ns[i] < ts[bs] / ns[bs]) bs = i;
+    for (size_t i = 1; i < mc.size(); ++i)
+        if (tm[i] / nm[i] < tm[bm] / nm[bm]) bm = i;
+    LaunchCfg best = mc[bm];
+    best.spawn_wpb = sc[bs].spawn_wpb;
+    best.spawn_grid = sc[bs].spawn_grid;
+    b->cfg = best;
     if (b->g1) cudaGraphExecDestroy(b->g1);
     if (b->g16) cudaGraphExecDestroy(b->g16);
     b->g1 = b->g16 = nullptr;
@@ -1466,6 +1506,21 @@ extern "C" int fq_run_autotune(fq_run* r, int steps) {
     r->tuned = r->single->cfg;
     r->has_tuned = true;
     return run_check(r);
+}
+
+extern "C" int fq_run_shape(fq_run* r, int* shape) {
+    if (!r || !shape || !r->seeded) return FQ_ERR_INVALID;
+    int rc = single_batch(r);
+    if (!rc) rc = batch_refresh(r->single);
+    if (rc) return rc;
+    const LaunchCfg& c = r->single->cfg;
+    shape[0] = c.spawn_wpb;
+    shape[1] = c.spawn_grid;
+    shape[2] = c.merge_wpb;
+    shape[3] = c.merge_grid;
+    shape[4] = (int)c.slots;
+    shape[5] = (int)c.scratch_slots;
+    return FQ_OK;
 }
 
 extern "C" int fq_run_profile(fq_run* r, int n, float* ms) {

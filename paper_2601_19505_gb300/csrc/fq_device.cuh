@@ -138,8 +138,11 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         if (r) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
-        const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        // one 32 x 32 -> 64-bit product gives both halves
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        const unsigned lo0 = (unsigned)p0, hi0 = (unsigned)(p0 >> 32);
+        const unsigned lo1 = (unsigned)p1, hi1 = (unsigned)(p1 >> 32);
         c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
     }
     return c;

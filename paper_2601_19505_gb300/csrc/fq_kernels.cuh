@@ -422,11 +422,23 @@ __device__ __forceinline__ u128 key_cas(u128* p, u128 cmp, u128 val) {
     return atomicCAS(p, cmp, val);
 }
 
+// home slot of `key` in a table of mask + 1 (a power of two) slots:
+// multiplicative (Fibonacci) hashing of the address folded to 32 bits.  The
+// keys of one bucket share the top bits of their segment hash, which this
+// hash does not use.
+__device__ __forceinline__ unsigned fold32(uint64_t k) { return (unsigned)k ^ (unsigned)(k >> 32); }
+__device__ __forceinline__ unsigned fold32(u128 k) {
+    return fold32((uint64_t)k ^ (uint64_t)(k >> 64));
+}
+template <class K> __device__ __forceinline__ unsigned table_home(K key, unsigned mask) {
+    return (fold32(key) * 0x9E3779B1u) >> (32 - __popc(mask));
+}
+
 // slot of `key`, inserting it if absent (is_new set); -1 when the table is full
 template <class K>
 __device__ __forceinline__ int table_insert(K* tkey, unsigned mask, K key, bool& is_new) {
     const K EMPTY = KeyOps<K>::empty();
-    unsigned q = (unsigned)fmix64(KeyOps<K>::rng_h(key)) & mask;
+    unsigned q = table_home(key, mask);
     is_new = false;
     for (unsigned probe = 0; probe <= mask; ++probe) {
         const K seen = tkey[q];
@@ -444,7 +456,7 @@ __device__ __forceinline__ int table_insert(K* tkey, unsigned mask, K key, bool&
 template <class K>
 __device__ __forceinline__ int table_find(const K* tkey, unsigned mask, K key) {
     const K EMPTY = KeyOps<K>::empty();
-    unsigned q = (unsigned)fmix64(KeyOps<K>::rng_h(key)) & mask;
+    unsigned q = table_home(key, mask);
     for (unsigned probe = 0; probe <= mask; ++probe) {
         const K seen = tkey[q];
         if (seen == key) return (int)q;

@@ -318,6 +318,13 @@ class Run:
             elif rc:
                 raise RunError(rc, "advance", self.error_bits())
 
+    def shape(self) -> dict:
+        """The launch shape the run steps with (fq_run_shape)."""
+        v = (C.c_int * 6)()
+        _check(self._lib.fq_run_shape(self.r, v), "fq_run_shape")
+        keys = ("spawn_wpb", "spawn_grid", "merge_wpb", "merge_grid", "slots", "scratch_slots")
+        return dict(zip(keys, [int(x) for x in v]))
+
     def profile(self, n: int):
         """Mean ms per step of (spawn, merge, shift) over n eagerly launched steps."""
         ms = (C.c_float * 3)()
