@@ -394,7 +394,9 @@ def gpu_arm(args, cfg, name):
             "dtype": DTYPE[cfg["mode"]], "data": "synthetic",
             "config": {"workload": describe(cfg, name), "equilibration_steps": equil,
                        "autotune_steps": tune_steps, "len_mean": L_mean,
-                       "spawns_mean": S_mean, "graph_replay": True,
+                       "spawns_mean": S_mean,
+                       "exact_columns_mean": float(hist["exact_steps"].mean()),
+                       "graph_replay": True,
                        "l2": "working set per step %.2f GB > 129 MB L2; no flush" % (ws / 1e9),
                        "parallelism": "replicas x%d" % world,
                        "launch_shape": run.shape()},

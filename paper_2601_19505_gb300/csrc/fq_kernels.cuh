@@ -133,7 +133,7 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     typedef typename MD::Col Col;
     typedef SpawnSmem<K, AMP, 32 * IPT> SM;
     constexpr int CH = 32 * IPT;
-    constexpr int U = 2;  // spawns per lane per round
+    constexpr int U = 1;  // spawns per lane per round
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     unsigned char* const wbase = smem + (size_t)wib * SM::bytes;
