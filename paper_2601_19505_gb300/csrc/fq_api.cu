@@ -393,8 +393,7 @@ static int ham_column_dev(const fq_ham* h, int amp, fq_key key, double* diag, fq
     CK(cudaMalloc((void**)&d_sq, sizeof(double) * (mp.kmax + 1)));
     CK(cudaMalloc((void**)&d_hop, sizeof(double) * (mp.kmax + 1)));
     CK(cudaMalloc((void**)&d_hop32, sizeof(float) * (mp.kmax + 1)));
-    k_tables<<<(unsigned)((mp.kmax + 256) / 256), 256, 0, s>>>(mp.t, mp.kmax, d_sq, d_hop, d_hop32,
-                                                               0, nullptr, nullptr);
+    k_tables<<<(unsigned)((mp.kmax + 256) / 256), 256, 0, s>>>(mp.t, mp.kmax, d_sq, d_hop, d_hop32);
     mp.sqrt_tab = d_sq;
     mp.hop_tab = d_hop;
     mp.hop32_tab = d_hop32;
@@ -464,8 +463,8 @@ static void fill_desc(const fq_run* r, RunDesc& d, unsigned seg_base) {
         d.norm_q = r->amp == FQ_AMP_INT || r->det ? 0 : std::ilogb(r->prm.threshold) - 52;
     }
     d.mmax = r->tab.mmax;
-    d.ratio64 = r->tab.r64;
-    d.ratio32 = r->tab.r32;
+    d.coef64 = r->tab.r64;
+    d.coef32 = r->tab.r32;
     d.smax = r->smax;
     d.fac64 = r->fac64;
     d.del32 = r->del32;
@@ -506,18 +505,21 @@ static cudaError_t sync_self(fq_run* r) {
 
 // a launch shape: persistent grids of one (spawn) or a few (merge) blocks per
 // SM, sized by occupancy; at most one warp per segment
-static LaunchCfg make_cfg(const KernelSet* ks, int spawn_wpb, int spawn_waves, int merge_wpb,
+static LaunchCfg make_cfg(const KernelSet* ks, int spawn_var, int spawn_waves, int merge_var,
                           unsigned slots, unsigned G) {
     LaunchCfg c;
+    const int spawn_wpb = variant_wpb(spawn_var), merge_wpb = variant_wpb(merge_var);
+    c.spawn_var = spawn_var;
     c.spawn_wpb = spawn_wpb;
+    c.merge_var = merge_var;
     c.merge_wpb = merge_wpb;
     c.slots = slots;
     c.scratch_slots = 0;
     c.scratch = nullptr;
     const int sms = num_sms();
-    int occ_s = ks->spawn_occupancy(spawn_wpb);
+    int occ_s = ks->spawn_occupancy(spawn_var);
     const size_t smem = (size_t)merge_wpb * slots * ks->slot_bytes;
-    int occ_m = ks->merge_occupancy(merge_wpb, smem);
+    int occ_m = ks->merge_occupancy(merge_var, smem);
     if (occ_s < 1) occ_s = 1;
     if (occ_m < 1) occ_m = 1;
     const long long ws = ((long long)G + spawn_wpb - 1) / spawn_wpb;
@@ -671,10 +673,9 @@ extern "C" int fq_run_create(fq_run** out, const fq_ham* h, const fq_params* p, 
     if (e == cudaSuccess) e = cudaMemsetAsync(r->sfill, 0, sizeof(unsigned) * B, r->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->ref_off, 0, sizeof(unsigned) * (B + 1), r->stream);
     if (e == cudaSuccess) {
-        const long long nt = std::max<long long>(r->tab.kmax + 1, (long long)nrat);
+        const long long nt = r->tab.kmax + 1;
         k_tables<<<(unsigned)((nt + 255) / 256), 256, 0, r->stream>>>(
-            h->mp.t, r->tab.kmax, r->tab.sq, r->tab.hop, r->tab.hop32, r->tab.mmax, r->tab.r64,
-            r->tab.r32);
+            h->mp.t, r->tab.kmax, r->tab.sq, r->tab.hop, r->tab.hop32);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
@@ -987,13 +988,13 @@ static int capture(fq_batch* b, int n, cudaGraphExec_t* out) {
 static std::vector<LaunchCfg> batch_shapes(fq_batch* b, unsigned slots) {
     std::vector<LaunchCfg> v;
     const size_t limit = 200u * 1024u;
-    v.push_back(make_cfg(b->ks, 8, 1, 8, slots, b->G));
-    for (int sw : {4, 8})
+    v.push_back(make_cfg(b->ks, 0, 1, 0, slots, b->G));
+    for (int sv = 0; sv < kKernelVariants; ++sv)
         for (int waves : {1, 2})
-            for (int mw : {4, 8})
+            for (int mv = 0; mv < kKernelVariants; ++mv)
                 for (unsigned sl : {slots / 2, slots, slots * 2}) {
-                    if (sl < 64 || (size_t)mw * sl * b->ks->slot_bytes > limit) continue;
-                    v.push_back(make_cfg(b->ks, sw, waves, mw, sl, b->G));
+                    if (sl < 64 || (size_t)variant_wpb(mv) * sl * b->ks->slot_bytes > limit) continue;
+                    v.push_back(make_cfg(b->ks, sv, waves, mv, sl, b->G));
                 }
     return v;
 }
@@ -1050,8 +1051,8 @@ static int batch_build(fq_batch* b) {
     if (nr == 1 && b->runs[0]->has_tuned) {
         const LaunchCfg& t = b->runs[0]->tuned;
         for (const LaunchCfg& c : b->shapes)
-            if (c.spawn_wpb == t.spawn_wpb && c.spawn_grid == t.spawn_grid &&
-                c.merge_wpb == t.merge_wpb && c.merge_grid == t.merge_grid && c.slots == t.slots)
+            if (c.spawn_var == t.spawn_var && c.spawn_grid == t.spawn_grid &&
+                c.merge_var == t.merge_var && c.merge_grid == t.merge_grid && c.slots == t.slots)
                 b->cfg = c;
     }
     int rc = capture(b, 1, &b->g1);
@@ -1434,9 +1435,9 @@ static int autotune(fq_batch* b, int steps) {
     std::vector<LaunchCfg> sc, mc;
     for (const LaunchCfg& c : b->shapes) {
         bool seen_s = false, seen_m = false;
-        for (const LaunchCfg& x : sc) seen_s |= x.spawn_wpb == c.spawn_wpb && x.spawn_grid == c.spawn_grid;
+        for (const LaunchCfg& x : sc) seen_s |= x.spawn_var == c.spawn_var && x.spawn_grid == c.spawn_grid;
         for (const LaunchCfg& x : mc)
-            seen_m |= x.merge_wpb == c.merge_wpb && x.merge_grid == c.merge_grid && x.slots == c.slots;
+            seen_m |= x.merge_var == c.merge_var && x.merge_grid == c.merge_grid && x.slots == c.slots;
         if (!seen_s) sc.push_back(c);
         if (!seen_m) mc.push_back(c);
     }
@@ -1449,6 +1450,7 @@ static int autotune(fq_batch* b, int steps) {
     auto shape = [&](size_t i) {
         LaunchCfg c = mc[i % mc.size()];
         const LaunchCfg& s2 = sc[i % sc.size()];
+        c.spawn_var = s2.spawn_var;
         c.spawn_wpb = s2.spawn_wpb;
         c.spawn_grid = s2.spawn_grid;
         return c;
@@ -1485,6 +1487,7 @@ static int autotune(fq_batch* b, int steps) {
     for (size_t i = 1; i < mc.size(); ++i)
         if (tm[i] / nm[i] < tm[bm] / nm[bm]) bm = i;
     LaunchCfg best = mc[bm];
+    best.spawn_var = sc[bs].spawn_var;
     best.spawn_wpb = sc[bs].spawn_wpb;
     best.spawn_grid = sc[bs].spawn_grid;
     b->cfg = best;

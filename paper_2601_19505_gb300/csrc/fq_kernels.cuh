@@ -47,10 +47,15 @@ template <> struct AmpT<FQ_AMP_INT> {
 template <> struct AmpT<FQ_AMP_F64> { typedef double A, S, ACC, C; };
 template <> struct AmpT<FQ_AMP_F32> { typedef float A, S, ACC, C; };
 
-// resident blocks per SM the spawn and merge kernels are compiled for: 8-warp
-// blocks get up to 128 registers a thread (16 warps per SM), 4-warp blocks
-// up to 80 (24 warps per SM); the autotuner picks between the two
-constexpr int min_blocks(int wpb) { return wpb >= 8 ? 2 : 6; }
+// compiled variants of the spawn and merge kernels (the autotuner picks one
+// of each): warps per block and the resident blocks per SM the registers
+// are capped for -- 8 x 2 (up to 128 registers a thread, 16 warps per SM),
+// 4 x 5 (up to 96, 20 warps), 4 x 6 (up to 80, 24 warps)
+template <int V> struct Var;
+template <> struct Var<0> { static constexpr int WPB = 8, MINB = 2; };
+template <> struct Var<1> { static constexpr int WPB = 4, MINB = 5; };
+template <> struct Var<2> { static constexpr int WPB = 4, MINB = 6; };
+constexpr int kVariants = 3;
 
 // ---------------------------------------------------------------------------
 // warp-level helpers
@@ -123,9 +128,10 @@ template <class K, int AMP, int CH> struct SpawnSmem {
     static constexpr size_t bytes = m_off + al(CH * sizeof(unsigned));
 };
 
-template <class K, int AMP, int KIND, int WPB, int IPT>
-__global__ void __launch_bounds__(WPB * 32, min_blocks(WPB))
+template <class K, int AMP, int KIND, int V, int IPT>
+__global__ void __launch_bounds__(Var<V>::WPB * 32, Var<V>::MINB)
 k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, unsigned G) {
+    constexpr int WPB = Var<V>::WPB;
     typedef typename AmpT<AMP>::A A;
     typedef typename AmpT<AMP>::S S;
     typedef typename AmpT<AMP>::C CO;
@@ -304,16 +310,15 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
                         coef[j] = (-(CO)dt) * c;
                     } else {
                         ++n_inex;
-                        CO ratio;
                         const int mmax = R->mmax;
                         if (KIND != FQ_KIND_MOM_1D && (int)m <= mmax && (int)ce <= mmax) {
+                            // (-dt) (m / n) from the run's table for this dt
                             const size_t ri = (size_t)m * (size_t)(mmax + 1) + ce;
-                            if constexpr (AMP == FQ_AMP_F32) ratio = __ldg(R->ratio32 + ri);
-                            else ratio = __ldg(R->ratio64 + ri);
+                            if constexpr (AMP == FQ_AMP_F32) coef[j] = R->coef32[ri] * c;
+                            else coef[j] = R->coef64[ri] * c;
                         } else {
-                            ratio = (CO)m / (CO)ce;
+                            coef[j] = ((-(CO)dt) * ((CO)m / (CO)ce)) * c;
                         }
-                        coef[j] = ((-(CO)dt) * ratio) * c;
                     }
                     wm[i] = m | (ex ? 0x80000000u : 0u);
                 }
@@ -775,10 +780,11 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
 //     whose spawns could exceed 0.7 SW uses the warp's table of SS slots in
 //     global scratch memory instead.  No block barriers.
 
-template <class K, int AMP, int KIND, int WPB>
-__global__ void __launch_bounds__(WPB * 32, min_blocks(WPB))
+template <class K, int AMP, int KIND, int V>
+__global__ void __launch_bounds__(Var<V>::WPB * 32, Var<V>::MINB)
 k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, unsigned G,
         unsigned SW, unsigned char* __restrict__ scratch, unsigned SS) {
+    constexpr int WPB = Var<V>::WPB;
     typedef typename AmpT<AMP>::ACC ACC;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -872,9 +878,21 @@ __device__ __forceinline__ void write_factors(const RunDesc* R, double S, double
     }
 }
 
+// ... and, when dt is set, the spawn coefficients (-dt) (m / n) per (m, n)
+// (m off-diagonal entries, n picks), in FP64 and in FP32 arithmetic
 static __global__ void k_factors(const RunDesc* __restrict__ runs) {
     const RunDesc* R = runs + blockIdx.x;
-    if (R->smax >= 0 && R->fac64) write_factors(R, R->st->shift, R->st->dt);
+    const double dt = R->st->dt;
+    if (R->smax >= 0 && R->fac64) write_factors(R, R->st->shift, dt);
+    if (R->coef64) {
+        const int w = R->mmax + 1;
+        const float dtf = (float)dt;
+        for (int i = threadIdx.x; i < w * w; i += blockDim.x) {
+            const int m = i / w, n = i % w;
+            R->coef64[i] = n ? (-dt) * ((double)m / (double)n) : 0.0;
+            R->coef32[i] = n ? (-dtf) * ((float)m / (float)n) : 0.0f;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -948,19 +966,13 @@ __global__ void __launch_bounds__(BLOCK) k_shift(const RunDesc* __restrict__ run
 
 // sqrt(k), -(t sqrt(k)) and its FP32 rounding for k <= kmax; m / n in FP64
 // and FP32 for 1 <= n <= m <= mmax
-static __global__ void k_tables(double t, int kmax, double* sq, double* hop, float* hop32, int mmax,
-                         double* r64, float* r32) {
+static __global__ void k_tables(double t, int kmax, double* sq, double* hop, float* hop32) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i <= kmax) {
         const double s = sqrt((double)i);
         sq[i] = s;
         hop[i] = -(t * s);
         hop32[i] = (float)hop[i];
-    }
-    if (r64 && i < (mmax + 1) * (mmax + 1)) {
-        const int m = i / (mmax + 1), n = i % (mmax + 1);
-        r64[i] = n ? (double)m / (double)n : 0.0;
-        r32[i] = n ? (float)m / (float)n : 0.0f;
     }
 }
 

@@ -15,53 +15,63 @@ template <class K, int AMP, int KIND> struct Launch {
     static constexpr size_t spawn_smem(int wpb) {
         return (size_t)wpb * SpawnSmem<K, AMP, 128>::bytes;
     }
+    template <int V> static void spawn_v(const LaunchCfg& c, const RunDesc* d, const unsigned* sr,
+                                         unsigned G, cudaStream_t s) {
+        constexpr int W = Var<V>::WPB;
+        k_spawn<K, AMP, KIND, V, 4><<<c.spawn_grid, W * 32, spawn_smem(W), s>>>(d, sr, G);
+    }
     static void spawn(const LaunchCfg& c, const RunDesc* d, const unsigned* sr, unsigned G,
                       cudaStream_t s) {
-        if (c.spawn_wpb == 4)
-            k_spawn<K, AMP, KIND, 4, 4><<<c.spawn_grid, 128, spawn_smem(4), s>>>(d, sr, G);
-        else
-            k_spawn<K, AMP, KIND, 8, 4><<<c.spawn_grid, 256, spawn_smem(8), s>>>(d, sr, G);
+        if (c.spawn_var == 1) spawn_v<1>(c, d, sr, G, s);
+        else if (c.spawn_var == 2) spawn_v<2>(c, d, sr, G, s);
+        else spawn_v<0>(c, d, sr, G, s);
+    }
+    template <int V> static void merge_v(const LaunchCfg& c, const RunDesc* d, const unsigned* sr,
+                                         unsigned G, cudaStream_t s) {
+        constexpr int W = Var<V>::WPB;
+        const size_t smem = (size_t)W * c.slots * slot_bytes<K, AMP>();
+        k_merge<K, AMP, KIND, V><<<c.merge_grid, W * 32, smem, s>>>(d, sr, G, c.slots, c.scratch,
+                                                                    c.scratch_slots);
     }
     static void merge(const LaunchCfg& c, const RunDesc* d, const unsigned* sr, unsigned G,
                       cudaStream_t s) {
-        const size_t smem = (size_t)c.merge_wpb * c.slots * slot_bytes<K, AMP>();
-        if (c.merge_wpb == 4)
-            k_merge<K, AMP, KIND, 4><<<c.merge_grid, 128, smem, s>>>(d, sr, G, c.slots, c.scratch,
-                                                                      c.scratch_slots);
-        else
-            k_merge<K, AMP, KIND, 8><<<c.merge_grid, 256, smem, s>>>(d, sr, G, c.slots, c.scratch,
-                                                                      c.scratch_slots);
+        if (c.merge_var == 1) merge_v<1>(c, d, sr, G, s);
+        else if (c.merge_var == 2) merge_v<2>(c, d, sr, G, s);
+        else merge_v<0>(c, d, sr, G, s);
     }
-    static cudaError_t prepare(size_t smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_merge<K, AMP, KIND, 4>,
+    template <int V> static cudaError_t prepare_v(size_t smem) {
+        cudaError_t e = cudaFuncSetAttribute(k_merge<K, AMP, KIND, V>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_merge<K, AMP, KIND, 8>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_spawn<K, AMP, KIND, 4, 4>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spawn_smem(4));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_spawn<K, AMP, KIND, 8, 4>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spawn_smem(8));
+            e = cudaFuncSetAttribute(k_spawn<K, AMP, KIND, V, 4>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)spawn_smem(Var<V>::WPB));
         return e;
     }
-    static int spawn_occupancy(int wpb) {
+    static cudaError_t prepare(size_t smem) {
+        cudaError_t e = prepare_v<0>(smem);
+        if (e == cudaSuccess) e = prepare_v<1>(smem);
+        if (e == cudaSuccess) e = prepare_v<2>(smem);
+        return e;
+    }
+    static int spawn_occupancy(int var) {
         int n = 0;
-        if (wpb == 4)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spawn<K, AMP, KIND, 4, 4>, 128,
-                                                          spawn_smem(4));
+        if (var == 1)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spawn<K, AMP, KIND, 1, 4>, 128, spawn_smem(4));
+        else if (var == 2)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spawn<K, AMP, KIND, 2, 4>, 128, spawn_smem(4));
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spawn<K, AMP, KIND, 8, 4>, 256,
-                                                          spawn_smem(8));
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spawn<K, AMP, KIND, 0, 4>, 256, spawn_smem(8));
         return n;
     }
-    static int merge_occupancy(int wpb, size_t smem) {
+    static int merge_occupancy(int var, size_t smem) {
         int n = 0;
-        if (wpb == 4)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_merge<K, AMP, KIND, 4>, 128, smem);
+        if (var == 1)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_merge<K, AMP, KIND, 1>, 128, smem);
+        else if (var == 2)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_merge<K, AMP, KIND, 2>, 128, smem);
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_merge<K, AMP, KIND, 8>, 256, smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_merge<K, AMP, KIND, 0>, 256, smem);
         return n;
     }
     static void scratch_init(unsigned char* scratch, unsigned slots, unsigned nwarps,

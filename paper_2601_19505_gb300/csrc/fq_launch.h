@@ -14,8 +14,8 @@ struct KernelSet {
     void (*spawn)(const LaunchCfg&, const RunDesc*, const unsigned*, unsigned, cudaStream_t);
     void (*merge)(const LaunchCfg&, const RunDesc*, const unsigned*, unsigned, cudaStream_t);
     cudaError_t (*prepare)(size_t merge_smem);
-    int (*spawn_occupancy)(int wpb);
-    int (*merge_occupancy)(int wpb, size_t smem);
+    int (*spawn_occupancy)(int var);               // resident blocks per SM
+    int (*merge_occupancy)(int var, size_t smem);
     void (*scratch_init)(unsigned char* scratch, unsigned slots, unsigned nwarps, cudaStream_t);
     void (*seed)(const RunDesc*, const void*, const double*, size_t, cudaStream_t);
     void (*gather_vec)(const void* keys, const void* amps, unsigned cap, const unsigned* cnt,
@@ -36,6 +36,10 @@ struct KernelSet {
 
 // kw = 64-bit words per address (1 or 2), amp = FQ_AMP_*, kind = FQ_KIND_*
 const KernelSet* kernel_set(int kw, int amp, int kind);
+
+// warps per block of the compiled kernel variants (fq_kernels.cuh, Var<V>)
+inline int variant_wpb(int var) { return var == 0 ? 8 : 4; }
+constexpr int kKernelVariants = 3;
 
 void launch_shift(const RunDesc* runs, int nruns, cudaStream_t s);
 

@@ -90,9 +90,9 @@ struct RunDesc {
     unsigned* sfill;
     RunState* st;
     StatsRow* hist;
-    int mmax;                 // largest m of the ratio table (real space)
-    const double* ratio64;    // (double)m / (double)n, index m * (mmax + 1) + n
-    const float* ratio32;     // (float)m / (float)n
+    int mmax;                 // largest m of the coefficient tables (real space)
+    double* coef64;           // (-dt) ((double)m / (double)n), index m * (mmax + 1) + n
+    float* coef32;            // the same in FP32 arithmetic
     int smax;                 // largest sum n(n-1) (real space)
     double* fac64;            // 1 + dt (S - H_ii) per s = sum n(n-1), this step
     float* del32;             // (float)(dt (S - H_ii)) per s, this step
@@ -107,9 +107,11 @@ struct RunDesc {
 };
 
 struct LaunchCfg {
-    int spawn_wpb;        // warps per spawn block (4 or 8)
+    int spawn_var;        // compiled variant of the spawn kernel (warps, register cap)
+    int spawn_wpb;        // its warps per block
     int spawn_grid;       // persistent spawn blocks
-    int merge_wpb;        // warps per merge block (4 or 8)
+    int merge_var;        // compiled variant of the merge kernel
+    int merge_wpb;        // its warps per block
     int merge_grid;       // persistent merge blocks
     unsigned slots;       // on-chip table slots per merge warp (power of 2)
     unsigned scratch_slots;       // global scratch table slots per merge warp
