@@ -139,7 +139,6 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     typedef typename MD::Col Col;
     typedef SpawnSmem<K, AMP, 32 * IPT> SM;
     constexpr int CH = 32 * IPT;
-    constexpr int U = 1;  // spawns per lane per round
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     unsigned char* const wbase = smem + (size_t)wib * SM::bytes;
@@ -151,51 +150,47 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     unsigned g0, g1;
     warp_range(G, blockIdx.x * WPB + wib, gridDim.x * WPB, g0, g1);
 
-    // the run of the current item and its per-step constants
+    // the run of the current item: its segments [run_lo, run_hi) and per-step
+    // constants
     const RunDesc* R = nullptr;
-    int cur_r = -1;
+    unsigned run_lo = 0, run_hi = 0;
     unsigned err = 0;
     const K* vk0 = nullptr;
     const A* va0 = nullptr;
     const unsigned* vcnt = nullptr;
-    unsigned Cv = 0, Cs = 0, seg_base = 0, stepno = 0;
+    unsigned Cv = 0, Cs = 0, stepno = 0;
     K* sk = nullptr;
     S* sv = nullptr;
     unsigned* sfill = nullptr;
     int log2B = 0;
     double dt = 0.0;
     uint2 rkey = make_uint2(0, 0);
-    unsigned long long n_ex = 0, n_inex = 0, n_sp = 0;
+    unsigned n_ex = 0, n_inex = 0, n_sp = 0;
 
-    // spawns whose bucket slot is being reserved (stored one round later)
-    K pd[U];
-    S pv[U];
-    unsigned pb[U], pp[U];
-    bool ph[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) ph[u] = false;
+    // the spawn whose bucket slot is being reserved (stored one spawn later)
+    K pd = KeyOps<K>::empty();
+    S pv = (S)0;
+    unsigned pb = 0, pp = 0;
+    bool ph = false;
 
     auto flush_pending = [&]() {
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (!ph[u]) continue;
-            if (pp[u] < Cs) {
-                sk[(size_t)pb[u] * Cs + pp[u]] = pd[u];
-                sv[(size_t)pb[u] * Cs + pp[u]] = pv[u];
-            } else {
-                atomicOr(&R->st->err, FQ_DERR_SPAWN_CAP);
-            }
-            ph[u] = false;
+        if (!ph) return;
+        if (pp < Cs) {
+            sk[(size_t)pb * Cs + pp] = pd;
+            sv[(size_t)pb * Cs + pp] = pv;
+        } else {
+            atomicOr(&R->st->err, FQ_DERR_SPAWN_CAP);
         }
+        ph = false;
     };
     auto flush_counts = [&]() {
-        n_ex = warp_sum(n_ex);
-        n_inex = warp_sum(n_inex);
-        n_sp = warp_sum(n_sp);
+        const unsigned long long a = warp_sum((unsigned long long)n_ex);
+        const unsigned long long i = warp_sum((unsigned long long)n_inex);
+        const unsigned long long p = warp_sum((unsigned long long)n_sp);
         if (lane == 0) {
-            if (n_ex) atomicAdd(&R->st->n_exact, n_ex);
-            if (n_inex) atomicAdd(&R->st->n_inexact, n_inex);
-            if (n_sp) atomicAdd(&R->st->n_spawns, n_sp);
+            if (a) atomicAdd(&R->st->n_exact, a);
+            if (i) atomicAdd(&R->st->n_inexact, i);
+            if (p) atomicAdd(&R->st->n_spawns, p);
         }
         n_ex = n_inex = n_sp = 0;
     };
@@ -206,7 +201,6 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
             flush_counts();
         }
         R = runs + r;
-        cur_r = r;
         // lane 0 reads, the warp shares: another warp may set an error bit
         unsigned e = 0, c = 0;
         if (lane == 0) {
@@ -215,12 +209,13 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
         }
         err = __shfl_sync(0xFFFFFFFFu, e, 0);
         const unsigned cur = __shfl_sync(0xFFFFFFFFu, c, 0);
+        run_lo = R->seg_base;
+        run_hi = run_lo + R->B;
         vk0 = (const K*)R->vkeys[cur];
         va0 = (const A*)R->vamps[cur];
         vcnt = R->vcount[cur];
         Cv = R->Cv;
         Cs = R->Cs;
-        seg_base = R->seg_base;
         sk = (K*)R->skeys;
         sv = (S*)R->samps;
         sfill = R->sfill;
@@ -229,22 +224,71 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
         stepno = (unsigned)(R->st->step + 1);
         rkey = make_uint2(R->key_x, R->key_y);
     };
-    // the next non-empty segment of the current run at or after g (g1 if none
-    // before the run changes or the range ends); n = its entry count
+    // the next non-empty segment of the current run at or after g; the end
+    // of the run's part of the range if none (n = its entry count)
     auto next_segment = [&](unsigned g, unsigned& n) -> unsigned {
-        for (; g < g1; ++g) {
-            if ((int)seg_run[g] != cur_r) return g;  // run change: handled by the caller
-            if (err) continue;
-            n = vcnt[g - seg_base];
+        const unsigned hi = min(g1, run_hi);
+        if (err) return hi;
+        for (; g < hi; ++g) {
+            n = vcnt[g - run_lo];
             if (n) return g;
         }
-        return g1;
+        return hi;
     };
     auto stage = [&](unsigned g, unsigned c0, unsigned cn, int b) {
-        const size_t e0 = (size_t)(g - seg_base) * Cv + c0;
+        const size_t e0 = (size_t)(g - run_lo) * Cv + c0;
         warp_copy_async(in_key + b * CH, vk0 + e0, cn * (unsigned)sizeof(K), lane);
         warp_copy_async(in_amp + b * CH, va0 + e0, cn * (unsigned)sizeof(A), lane);
         cp_async_commit();
+    };
+    // attempt a of a source (key, coefficient cf, mm = m and flags): the
+    // destination and value; false when an integer spawn rounds to nothing
+    auto make = [&](K key, CO cf, unsigned mm, unsigned a, K& dest, S& val) -> bool {
+        const ModelParams& mp = R->mp;
+        const unsigned m = mm & 0x3FFFFFFFu;
+        const bool ex = (AMP != FQ_AMP_INT) && (mm >> 31);
+        Col col;
+        if constexpr (KIND != FQ_KIND_MOM_1D) col.n_occ = (int)(m / (unsigned)MD::Z);
+        else MD::num_offdiag(mp, key, col);
+        uint4 w = make_uint4(0, 0, 0, 0);
+        unsigned kk = a;
+        if (!ex) {
+            w = draw(rkey, stepno, a, KeyOps<K>::rng_h(key));
+            kk = pick(w, m);
+        }
+        if constexpr (AMP == FQ_AMP_INT) {
+            double hv;
+            dest = MD::offdiag(mp, key, col, kk, hv);
+            const double p = fabs(hv) * cf;
+            const double fl = floor(p);
+            const long long nw = (long long)fl + (uniform53(w) < p - fl ? 1 : 0);
+            if (!nw) return false;
+            const int sg = (hv > 0.0 ? -1 : 1) * ((mm & 0x40000000u) ? -1 : 1);
+            val = (S)(sg * nw);
+        } else {
+            CO hv;
+            dest = MD::offdiag(mp, key, col, kk, hv);
+            val = hv * cf;
+        }
+        return true;
+    };
+    // reserve a bucket slot for this lane's spawn (if any) and store the
+    // previous one, whose slot has arrived meanwhile
+    auto emit = [&](bool has, K dest, S val) {
+        unsigned bk = 0, pos = 0;
+        if (has) {
+            bk = segment_of(fmix64(KeyOps<K>::rng_h(dest)), log2B);
+            pos = atomicAdd(&sfill[bk], 1u);
+            ++n_sp;
+        }
+        flush_pending();
+        if (has) {
+            pd = dest;
+            pv = val;
+            pb = bk;
+            pp = pos;
+            ph = true;
+        }
     };
 
     // current item (segment g, entries [c0, c0 + CH) of n), staged in buffer b
@@ -252,14 +296,14 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     int b = 0;
     bool staged = false;
     while (true) {
-        if (g < g1 && (int)seg_run[g] != cur_r) {
+        if (g < g1 && (g < run_lo || g >= run_hi)) {
             enter_run((int)seg_run[g]);
             staged = false;
         }
         if (!staged) {
             g = next_segment(g, n);
             if (g >= g1) break;
-            if ((int)seg_run[g] != cur_r) continue;
+            if (g >= run_hi) continue;
             c0 = 0;
             stage(g, 0, min((unsigned)CH, n), b);
         }
@@ -272,21 +316,23 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
             nc0 = 0;
             ng = next_segment(g + 1, nn);
         }
-        staged = ng < g1 && (int)seg_run[ng] == cur_r;
+        staged = ng < g1 && ng < run_hi;
         if (staged) stage(ng, nc0, min((unsigned)CH, nn - nc0), b ^ 1);
 
         const K* wkey = in_key + b * CH;
         const A* wamp = in_amp + b * CH;
         const ModelParams& mp = R->mp;
-        unsigned cnt[IPT], tsum = 0;
-        CO coef[IPT];
-#pragma unroll
+        // sources i = j * 32 + lane: the decision, the coefficient and the
+        // first attempt at once; further attempts are counted (extras) and
+        // dealt out below
+        unsigned xoff = 0;
         for (int j = 0; j < IPT; ++j) {
-            const unsigned i = lane * IPT + j;
-            unsigned c_i = 0;
-            coef[j] = (CO)0;
+            const unsigned i = (unsigned)j * 32u + (unsigned)lane;
+            unsigned cnt = 0, mm = 0;
+            CO cf = (CO)0;
+            K key = KeyOps<K>::empty();
             if (i < cn) {
-                const K key = wkey[i];
+                key = wkey[i];
                 const CO c = (CO)wamp[i];
                 Col col;
                 const unsigned m = MD::num_offdiag(mp, key, col);
@@ -295,117 +341,65 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
                 if (AMP == FQ_AMP_INT) {
                     // integer walkers: |c| attempts, never an exact column;
                     // the coefficient is dt m (spawn probability per |H_ji|)
-                    c_i = m ? fl : 0u;
+                    cnt = m ? fl : 0u;
                     ++n_inex;
-                    coef[j] = (CO)(dt * (double)m);
-                    wm[i] = m | (c < (CO)0 ? 0x40000000u : 0u);
+                    cf = (CO)(dt * (double)m);
+                    mm = m | (c < (CO)0 ? 0x40000000u : 0u);
                 } else {
                     bool ex;
                     if (R->mode_det) ex = true;
                     else if (R->trel_one) ex = fl >= m;  // |c| >= m for an integer m
                     else ex = fabs((double)c) * R->t_rel >= (double)m;
-                    c_i = ex ? m : ce;
+                    cnt = ex ? m : ce;
                     if (ex) {
                         ++n_ex;
-                        coef[j] = (-(CO)dt) * c;
+                        cf = (-(CO)dt) * c;
                     } else {
                         ++n_inex;
                         const int mmax = R->mmax;
                         if (KIND != FQ_KIND_MOM_1D && (int)m <= mmax && (int)ce <= mmax) {
                             // (-dt) (m / n) from the run's table for this dt
                             const size_t ri = (size_t)m * (size_t)(mmax + 1) + ce;
-                            if constexpr (AMP == FQ_AMP_F32) coef[j] = R->coef32[ri] * c;
-                            else coef[j] = R->coef64[ri] * c;
+                            if constexpr (AMP == FQ_AMP_F32) cf = R->coef32[ri] * c;
+                            else cf = R->coef64[ri] * c;
                         } else {
-                            coef[j] = ((-(CO)dt) * ((CO)m / (CO)ce)) * c;
+                            cf = ((-(CO)dt) * ((CO)m / (CO)ce)) * c;
                         }
                     }
-                    wm[i] = m | (ex ? 0x80000000u : 0u);
+                    mm = m | (ex ? 0x80000000u : 0u);
                 }
+                wcoef[i] = cf;
+                wm[i] = mm;
             }
-            cnt[j] = c_i;
-            tsum += c_i;
+            const unsigned x = cnt > 1u ? cnt - 1u : 0u;
+            const unsigned incl = warp_incl_scan(x, lane);
+            woff[i] = xoff + incl - x;
+            xoff += __shfl_sync(0xFFFFFFFFu, incl, 31);
+            K dest = KeyOps<K>::empty();
+            S val = (S)0;
+            const bool has = cnt >= 1u && make(key, cf, mm, 0u, dest, val);
+            emit(has, dest, val);
         }
-        const unsigned incl = warp_incl_scan(tsum, lane);
-        const unsigned total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        unsigned off = incl - tsum;
-#pragma unroll
-        for (int j = 0; j < IPT; ++j) {
-            woff[lane * IPT + j] = off;
-            wcoef[lane * IPT + j] = coef[j];
-            off += cnt[j];
-        }
-        if (lane == 31) woff[CH] = total;
         __syncwarp();
-
-        for (unsigned q0 = 0; q0 < total; q0 += 32 * U) {
-            K dest[U];
-            S val[U];
-            unsigned bk[U];
-            bool has[U];
+        // attempts 1.. of every source, balanced over the lanes: spawn q
+        // belongs to the last source whose offset is <= q
+        for (unsigned q0 = 0; q0 < xoff; q0 += 32) {
+            const unsigned q = q0 + (unsigned)lane;
+            K dest = KeyOps<K>::empty();
+            S val = (S)0;
+            bool has = false;
+            if (q < xoff) {
+                unsigned i = 0;
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const unsigned q = q0 + u * 32 + lane;
-                has[u] = false;
-                if (q >= total) continue;
-                int i = 0;
-#pragma unroll
-                for (int st = CH / 2; st >= 1; st >>= 1)
+                for (unsigned st = CH / 2; st >= 1; st >>= 1)
                     if (woff[i + st] <= q) i += st;
-                const unsigned a = q - woff[i];
-                const K key = wkey[i];
-                const CO cf = wcoef[i];
-                const unsigned mm = wm[i];
-                const unsigned m = mm & 0x3FFFFFFFu;
-                const bool ex = (AMP != FQ_AMP_INT) && (mm >> 31);
-                Col col;
-                if constexpr (KIND != FQ_KIND_MOM_1D) col.n_occ = (int)(m / (unsigned)MD::Z);
-                else MD::num_offdiag(mp, key, col);
-                uint4 w = make_uint4(0, 0, 0, 0);
-                unsigned kk = a;
-                if (!ex) {
-                    w = draw(rkey, stepno, a, KeyOps<K>::rng_h(key));
-                    kk = pick(w, m);
-                }
-                if constexpr (AMP == FQ_AMP_INT) {
-                    double hv;
-                    dest[u] = MD::offdiag(mp, key, col, kk, hv);
-                    const double p = fabs(hv) * cf;
-                    const double fl = floor(p);
-                    const long long nw = (long long)fl + (uniform53(w) < p - fl ? 1 : 0);
-                    if (!nw) continue;
-                    const int sg = (hv > 0.0 ? -1 : 1) * ((mm & 0x40000000u) ? -1 : 1);
-                    val[u] = (S)(sg * nw);
-                } else {
-                    CO hv;
-                    dest[u] = MD::offdiag(mp, key, col, kk, hv);
-                    val[u] = hv * cf;
-                }
-                has[u] = true;
-                bk[u] = segment_of(fmix64(KeyOps<K>::rng_h(dest[u])), log2B);
+                has = make(wkey[i], wcoef[i], wm[i], 1u + (q - woff[i]), dest, val);
             }
-            unsigned pos[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (has[u]) pos[u] = atomicAdd(&sfill[bk[u]], 1u);
-            flush_pending();  // the previous round's slots have arrived by now
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (!has[u]) continue;
-                ++n_sp;
-                pd[u] = dest[u];
-                pv[u] = val[u];
-                pb[u] = bk[u];
-                pp[u] = pos[u];
-                ph[u] = true;
-            }
+            emit(has, dest, val);
         }
         __syncwarp();  // every lane is done with buffer b
-        if (!staged) {
-            g = ng;
-            continue;
-        }
         g = ng;
+        if (!staged) continue;
         c0 = nc0;
         n = nn;
         b ^= 1;
@@ -808,20 +802,20 @@ k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     warp_range(G, gw, gridDim.x * WPB, g0, g1);
 
     const RunDesc* R = nullptr;
-    int cur_r = -1;
+    unsigned run_lo = 0, run_hi = 0;  // segments of the current run
     unsigned err = 0, cur = 0;
     MergeAcc acc = {0, 0, 0, 0.0, false, false, false};
 
     for (unsigned g = g0; g < g1; ++g) {
-        const int r = (int)seg_run[g];
-        if (r != cur_r) {  // warp-uniform
+        if (g < run_lo || g >= run_hi) {  // warp-uniform
             if (R) {
                 merge_flush(R, acc.nlo, acc.nhi, acc.nlen, acc.nfp, acc.full, acc.over,
                             acc.range_bad, lane);
                 acc = MergeAcc{0, 0, 0, 0.0, false, false, false};
             }
-            R = runs + r;
-            cur_r = r;
+            R = runs + seg_run[g];
+            run_lo = R->seg_base;
+            run_hi = run_lo + R->B;
             // lane 0 reads, the warp shares: another warp may set an error bit
             unsigned e = 0, c = 0;
             if (lane == 0) {
