@@ -100,6 +100,14 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, unsigned 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// L2 prefetch of `bytes` rounded up to 16 at a 16-byte aligned address,
+// never past `cap` bytes (a multiple of 16: the region's capacity)
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes, unsigned cap) {
+    bytes = min((bytes + 15u) & ~15u, cap);
+    if (bytes)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // a warp copies `bytes` from global (16-byte aligned) to shared
 __device__ __forceinline__ void warp_copy_async(void* dst, const void* src, unsigned bytes, int lane) {
     for (unsigned o = (unsigned)lane * 16u; o < bytes; o += 32u * 16u)
@@ -226,11 +234,13 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     };
     // the next non-empty segment of the current run at or after g; the end
     // of the run's part of the range if none (n = its entry count)
+    // the count of segment pre_g, loaded one segment ahead of its use
+    unsigned pre_g = 0xFFFFFFFFu, pre_n = 0;
     auto next_segment = [&](unsigned g, unsigned& n) -> unsigned {
         const unsigned hi = min(g1, run_hi);
         if (err) return hi;
         for (; g < hi; ++g) {
-            n = vcnt[g - run_lo];
+            n = g == pre_g ? pre_n : vcnt[g - run_lo];
             if (n) return g;
         }
         return hi;
@@ -318,6 +328,10 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
         }
         staged = ng < g1 && ng < run_hi;
         if (staged) stage(ng, nc0, min((unsigned)CH, nn - nc0), b ^ 1);
+        if (staged && ng + 1 < min(g1, run_hi) && pre_g != ng + 1) {
+            pre_g = ng + 1;
+            pre_n = vcnt[pre_g - run_lo];
+        }
 
         const K* wkey = in_key + b * CH;
         const A* wamp = in_amp + b * CH;
@@ -805,6 +819,9 @@ k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     unsigned run_lo = 0, run_hi = 0;  // segments of the current run
     unsigned err = 0, cur = 0;
     MergeAcc acc = {0, 0, 0, 0.0, false, false, false};
+    // counts of buckets ahead_g and ahead2_g, loaded before they are needed
+    unsigned ahead_g = 0xFFFFFFFFu, ahead2_g = 0xFFFFFFFFu;
+    unsigned a1_old = 0, a1_sp = 0, a2_old = 0, a2_sp = 0;
 
     for (unsigned g = g0; g < g1; ++g) {
         if (g < run_lo || g >= run_hi) {  // warp-uniform
@@ -827,8 +844,52 @@ k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
         }
         if (err) continue;
         const unsigned seg = g - R->seg_base;
-        const unsigned n_old = R->vcount[cur][seg];
-        const unsigned n_sp = R->sfill[seg];
+        // this bucket's counts (loaded one bucket ahead when it was the next);
+        // then the next bucket's data is prefetched into L2 and the counts of
+        // the one after it are loaded
+        unsigned n_old, n_sp;
+        if (g == ahead_g) {
+            n_old = a1_old;
+            n_sp = a1_sp;
+        } else {
+            n_old = R->vcount[cur][seg];
+            n_sp = R->sfill[seg];
+        }
+        const unsigned g_end = min(g1, R->seg_base + R->B);
+        if (g + 1 < g_end) {
+            unsigned o1, s1;
+            if (g + 1 == ahead2_g) {
+                o1 = a2_old;
+                s1 = a2_sp;
+            } else {
+                o1 = R->vcount[cur][seg + 1];
+                s1 = R->sfill[seg + 1];
+            }
+            if (lane == 0) {
+                typedef typename AmpT<AMP>::A A;
+                typedef typename AmpT<AMP>::S S;
+                const size_t vo = (size_t)(seg + 1) * R->Cv, so = (size_t)(seg + 1) * R->Cs;
+                // capacities are multiples of 32 entries; sizes kept below 2^30
+                const unsigned Cv = min(R->Cv, 1u << 25), Cs = min(R->Cs, 1u << 25);
+                const unsigned po = min(o1, Cv), ps = min(s1, Cs);
+                prefetch_l2((const K*)R->vkeys[cur] + vo, po * (unsigned)sizeof(K),
+                            Cv * (unsigned)sizeof(K));
+                prefetch_l2((const A*)R->vamps[cur] + vo, po * (unsigned)sizeof(A),
+                            Cv * (unsigned)sizeof(A));
+                prefetch_l2((const K*)R->skeys + so, ps * (unsigned)sizeof(K),
+                            Cs * (unsigned)sizeof(K));
+                prefetch_l2((const S*)R->samps + so, ps * (unsigned)sizeof(S),
+                            Cs * (unsigned)sizeof(S));
+            }
+            ahead_g = g + 1;
+            a1_old = o1;
+            a1_sp = s1;
+            if (g + 2 < g_end) {
+                ahead2_g = g + 2;
+                a2_old = R->vcount[cur][seg + 2];
+                a2_sp = R->sfill[seg + 2];
+            }
+        }
         // the table holds the bucket's spawned addresses only
         const unsigned long long load = n_sp;
         if (load * 10ull <= (unsigned long long)SW * 7ull) {
