@@ -288,6 +288,16 @@ extern "C" int fq_ham_create(fq_ham** out, int kind, int Lx, int Ly, int N, doub
     mp.kind = kind; mp.M = M; mp.N = N; mp.Lx = Lx; mp.Ly = Ly; mp.nbits = N + M - 1;
     mp.t = t; mp.u = u;
     mp.g = u / (double)(2 * M);
+    if (kind != FQ_BH_MOM_1D) {
+        // directions (+x, -x, +y, -y) on the periodic lattice, site x + Lx y
+        for (int s2 = 0; s2 < M; ++s2) {
+            const int x = s2 % Lx, y = s2 / Lx;
+            mp.nbr[0][s2] = (unsigned char)((x + 1) % Lx + Lx * y);
+            mp.nbr[1][s2] = (unsigned char)((x + Lx - 1) % Lx + Lx * y);
+            mp.nbr[2][s2] = (unsigned char)(x + Lx * ((y + 1) % Ly));
+            mp.nbr[3][s2] = (unsigned char)(x + Lx * ((y + Ly - 1) % Ly));
+        }
+    }
     if (kind == FQ_BH_MOM_1D) {
         // mode j (1-based) carries k_j = 2 pi (j - floor(M/2)) / M
         for (int m = 0; m < M; ++m) {

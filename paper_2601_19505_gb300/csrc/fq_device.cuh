@@ -185,16 +185,6 @@ template <int KIND> struct Model;
 template <int KIND> struct RealModel {
     static constexpr int Z = KIND == FQ_KIND_REAL_1D ? 2 : 4;
 
-    __device__ __forceinline__ static int neighbour(const ModelParams& p, int s, int d) {
-        if (KIND == FQ_KIND_REAL_1D) return d == 0 ? (s + 1 == p.M ? 0 : s + 1) : (s == 0 ? p.M - 1 : s - 1);
-        int x = s % p.Lx, y = s / p.Lx;
-        if (d == 0) x = x + 1 == p.Lx ? 0 : x + 1;
-        else if (d == 1) x = x == 0 ? p.Lx - 1 : x - 1;
-        else if (d == 2) y = y + 1 == p.Ly ? 0 : y + 1;
-        else y = y == 0 ? p.Ly - 1 : y - 1;
-        return x + p.Lx * y;
-    }
-
     struct Col {  // per-source data reused by every pick of a column
         int n_occ;
     };
@@ -258,14 +248,32 @@ template <int KIND> struct RealModel {
             else val = __ldg(p.hop_tab + ns * (nt + 1));
             return dest;
         }
-        const int s = P - KeyOps<K>::popc(key & KeyOps<K>::low(P));
+        // 2D: the neighbouring site from the model's table; a hop to the
+        // next or previous site moves one separator (as in 1D), any other
+        // removes a one-bit at P and inserts one at the start of the target
+        // run, located once
+        typedef KeyOps<K> O;
+        const int s = P - O::popc(key & O::low(P));
         const int ns = run_from(key, P);
-        const int s2 = neighbour(p, s, d);
-        const int nt = mode_occ(key, s2);
+        const int s2 = p.nbr[d][s];
+        int nt;
+        K dest;
+        if (s2 == s + 1) {
+            nt = run_from(key, P + ns + 1);
+            dest = key ^ ((K)3 << (P + ns - 1));
+        } else if (s2 == s - 1) {
+            const K z = ~key & O::low(P - 1);
+            nt = z ? (P - 2 - (O::W - 1 - clz_k(z))) : (P - 1);
+            dest = key ^ ((K)3 << (P - 1));
+        } else {
+            const int q = mode_start(key, s2);
+            nt = run_from(key, q);
+            dest = ins_one(del_bit(key, P), q - (s2 > s ? 1 : 0));
+        }
         // -(t sqrt(n_s (n_s' + 1))) from the table
         if constexpr (sizeof(V) == 4) val = __ldg(p.hop32_tab + ns * (nt + 1));
         else val = __ldg(p.hop_tab + ns * (nt + 1));
-        return add_boson(del_bit(key, P), s2);
+        return dest;
     }
     // sum over modes of n (n - 1), so H_ii = (u/2) times this: windows of
     // w >= 2 consecutive one-bits lie inside one mode's run, and a run of n

@@ -37,6 +37,7 @@ struct ModelParams {
     const double* hop_tab;           // -(t * sqrt((double)k)), k <= kmax (device)
     const float* hop32_tab;          // (float) of hop_tab
     double eps[FQ_MAX_MOM_MODES];    // momentum-space single-particle energies
+    unsigned char nbr[4][128];       // real space: neighbour of site s in direction d
 };
 
 // One row of the time series; layout identical to fq_stats in fciqmc.h.
