@@ -49,7 +49,7 @@ UNIT = "configs/s"
 MODE_CODE = {"INT": 0, "REAL64": 1, "REAL32": 2, "DETERMINISTIC": 3}
 DTYPE = {"INT": "int64", "REAL64": "f64", "REAL32": "f32", "DETERMINISTIC": "f64"}
 # bytes fq_run_stats copies back per call: the error word and the run state
-STATS_D2H_BYTES = 4 + 144
+STATS_D2H_BYTES = 4 + 176  # the error word, then the 176-byte run state
 KERNEL_FILES = ["fq_kernels.cuh", "fq_device.cuh", "fq_shared.h"]
 
 
