@@ -378,6 +378,21 @@ extern "C" int fq_ham_starting_address(const fq_ham* h, fq_key* out) {
     return fq_encode(h, occ.data(), out);
 }
 
+// device buffers of one call, released on every return path
+struct CallBufs {
+    std::vector<void*> p;
+    ~CallBufs() {
+        for (void* q : p) cudaFree(q);
+    }
+    template <class T> cudaError_t get(T** out, size_t bytes) {
+        void* q = nullptr;
+        const cudaError_t e = cudaMalloc(&q, bytes);
+        if (e == cudaSuccess) p.push_back(q);
+        *out = (T*)q;
+        return e;
+    }
+};
+
 static int ham_column_dev(const fq_ham* h, int amp, fq_key key, double* diag, fq_key* dest,
                           double* val, size_t cap, size_t* m_out, cudaStream_t s) {
     int ndev = 0;
@@ -385,30 +400,30 @@ static int ham_column_dev(const fq_ham* h, int amp, fq_key key, double* diag, fq
     const KernelSet* ks = kernel_set(h->kw, amp, h->mp.kind);
     const size_t kb = ks->key_bytes;
     const unsigned ccap = (unsigned)std::min<size_t>(cap, 1u << 20);
-    void* d_key = nullptr;
+    CallBufs bufs;
     void* d_dest = nullptr;
     double *d_val = nullptr, *d_diag = nullptr;
     unsigned* d_m = nullptr;
-    CK(cudaMalloc(&d_key, kb));
-    CK(cudaMalloc(&d_dest, kb * (ccap ? ccap : 1)));
-    CK(cudaMalloc(&d_val, sizeof(double) * (ccap ? ccap : 1)));
-    CK(cudaMalloc(&d_diag, sizeof(double)));
-    CK(cudaMalloc(&d_m, sizeof(unsigned)));
+    CK(bufs.get(&d_dest, kb * (ccap ? ccap : 1)));
+    CK(bufs.get(&d_val, sizeof(double) * (ccap ? ccap : 1)));
+    CK(bufs.get(&d_diag, sizeof(double)));
+    CK(bufs.get(&d_m, sizeof(unsigned)));
     unsigned char kbuf[16];
     memcpy(kbuf, &key, 16);
     ModelParams mp = h->mp;
     mp.kmax = (mp.N + 1) * (mp.N + 2);
     double *d_sq = nullptr, *d_hop = nullptr;
     float* d_hop32 = nullptr;
-    CK(cudaMalloc((void**)&d_sq, sizeof(double) * (mp.kmax + 1)));
-    CK(cudaMalloc((void**)&d_hop, sizeof(double) * (mp.kmax + 1)));
-    CK(cudaMalloc((void**)&d_hop32, sizeof(float) * (mp.kmax + 1)));
+    CK(bufs.get(&d_sq, sizeof(double) * (mp.kmax + 1)));
+    CK(bufs.get(&d_hop, sizeof(double) * (mp.kmax + 1)));
+    CK(bufs.get(&d_hop32, sizeof(float) * (mp.kmax + 1)));
     k_tables<<<(unsigned)((mp.kmax + 256) / 256), 256, 0, s>>>(mp.t, mp.kmax, d_sq, d_hop, d_hop32);
     mp.sqrt_tab = d_sq;
     mp.hop_tab = d_hop;
     mp.hop32_tab = d_hop32;
     ks->column(mp, kbuf, d_dest, d_val, ccap, d_diag, d_m, s);
-    cudaError_t e = cudaStreamSynchronize(s);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     unsigned m = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&m, d_m, sizeof m, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && diag) e = cudaMemcpy(diag, d_diag, sizeof(double), cudaMemcpyDeviceToHost);
@@ -423,8 +438,6 @@ static int ham_column_dev(const fq_ham* h, int amp, fq_key key, double* diag, fq
             dest[i] = k;
         }
     }
-    cudaFree(d_key); cudaFree(d_dest); cudaFree(d_val); cudaFree(d_diag); cudaFree(d_m);
-    cudaFree(d_sq); cudaFree(d_hop); cudaFree(d_hop32);
     if (m_out) *m_out = m;
     return cuda_err(e);
 }
@@ -767,8 +780,9 @@ extern "C" int fq_run_seed(fq_run* r, const fq_key* keys, const double* amps, si
     pack_keys(sk.data(), m, kb, kbuf);
     void* d_k = nullptr;
     double* d_a = nullptr;
-    CK(cudaMalloc(&d_k, kb * (m ? m : 1)));
-    CK(cudaMalloc((void**)&d_a, sizeof(double) * (m ? m : 1)));
+    CallBufs bufs;  // released on every return
+    CK(bufs.get(&d_k, kb * (m ? m : 1)));
+    CK(bufs.get(&d_a, sizeof(double) * (m ? m : 1)));
     RunState s0;
     memset(&s0, 0, sizeof s0);
     CK(cudaMemcpy(&s0, r->st, sizeof s0, cudaMemcpyDeviceToHost));
@@ -802,8 +816,6 @@ extern "C" int fq_run_seed(fq_run* r, const fq_key* keys, const double* amps, si
     if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
     unsigned err = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&err, &r->st->err, sizeof err, cudaMemcpyDeviceToHost);
-    cudaFree(d_k);
-    cudaFree(d_a);
     if (e != cudaSuccess) return cuda_err(e);
     if (err) {
         unsigned z = 0;
@@ -839,9 +851,10 @@ extern "C" int fq_run_set_reference(fq_run* r, const fq_key* keys, const double*
     void *d_refs = nullptr, *d_tk = nullptr;
     double *d_y = nullptr, *d_th = nullptr, *d_tv = nullptr;
     unsigned *d_cnt = nullptr, *d_off = nullptr, *d_tseg = nullptr;
-    CK(cudaMalloc(&d_refs, kb * n));
-    CK(cudaMalloc((void**)&d_y, sizeof(double) * n));
-    CK(cudaMalloc((void**)&d_cnt, sizeof(unsigned) * n));
+    CallBufs bufs;  // released on every return
+    CK(bufs.get(&d_refs, kb * n));
+    CK(bufs.get(&d_y, sizeof(double) * n));
+    CK(bufs.get(&d_cnt, sizeof(unsigned) * n));
     CK(cudaMemcpy(d_refs, kbuf.data(), kb * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_y, y, sizeof(double) * n, cudaMemcpyHostToDevice));
     const ModelParams mp = run_mp(r);
@@ -850,11 +863,11 @@ extern "C" int fq_run_set_reference(fq_run* r, const fq_key* keys, const double*
     CK(cudaMemcpy(cnt.data(), d_cnt, sizeof(unsigned) * n, cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < n; ++i) off[i + 1] = off[i] + cnt[i];
     const size_t T = off[n];
-    CK(cudaMalloc((void**)&d_off, sizeof(unsigned) * (n + 1)));
-    CK(cudaMalloc(&d_tk, kb * T));
-    CK(cudaMalloc((void**)&d_th, sizeof(double) * T));
-    CK(cudaMalloc((void**)&d_tv, sizeof(double) * T));
-    CK(cudaMalloc((void**)&d_tseg, sizeof(unsigned) * T));
+    CK(bufs.get(&d_off, sizeof(unsigned) * (n + 1)));
+    CK(bufs.get(&d_tk, kb * T));
+    CK(bufs.get(&d_th, sizeof(double) * T));
+    CK(bufs.get(&d_tv, sizeof(double) * T));
+    CK(bufs.get(&d_tseg, sizeof(unsigned) * T));
     CK(cudaMemcpy(d_off, off.data(), sizeof(unsigned) * (n + 1), cudaMemcpyHostToDevice));
     r->ks->ref_terms(mp, d_refs, d_y, (int)n, d_off, d_tk, d_th, d_tv, d_tseg, r->log2B, 0);
     CK(cudaDeviceSynchronize());
@@ -865,8 +878,6 @@ extern "C" int fq_run_set_reference(fq_run* r, const fq_key* keys, const double*
     CK(cudaMemcpy(th.data(), d_th, sizeof(double) * T, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(tv.data(), d_tv, sizeof(double) * T, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(tseg.data(), d_tseg, sizeof(unsigned) * T, cudaMemcpyDeviceToHost));
-    cudaFree(d_refs); cudaFree(d_y); cudaFree(d_cnt); cudaFree(d_off);
-    cudaFree(d_tk); cudaFree(d_th); cudaFree(d_tv); cudaFree(d_tseg);
     // group the terms by segment (stable), so each merge block finds its own
     std::vector<size_t> order(T);
     for (size_t i = 0; i < T; ++i) order[i] = i;
@@ -1212,9 +1223,10 @@ static int gather(fq_run* r, const void* keys, const void* vals, unsigned cap, c
     unsigned* d_off = nullptr;
     void* d_k = nullptr;
     double* d_v = nullptr;
-    CK(cudaMalloc((void**)&d_off, sizeof(unsigned) * (B + 1)));
-    CK(cudaMalloc(&d_k, kb * T));
-    CK(cudaMalloc((void**)&d_v, sizeof(double) * T));
+    CallBufs bufs;  // released on every return
+    CK(bufs.get(&d_off, sizeof(unsigned) * (B + 1)));
+    CK(bufs.get(&d_k, kb * T));
+    CK(bufs.get(&d_v, sizeof(double) * T));
     CK(cudaMemcpy(d_off, off.data(), sizeof(unsigned) * (B + 1), cudaMemcpyHostToDevice));
     if (spawns) r->ks->gather_spawns(keys, vals, cap, cnt_dev, d_off, B, d_k, d_v, 0);
     else r->ks->gather_vec(keys, vals, cap, cnt_dev, d_off, B, d_k, d_v, nullptr, 0);
@@ -1223,7 +1235,6 @@ static int gather(fq_run* r, const void* keys, const void* vals, unsigned cap, c
     CK(cudaMemcpy(kbuf.data(), d_k, kb * T, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(ov.data(), d_v, sizeof(double) * T, cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < T; ++i) memcpy(&ok[i], kbuf.data() + i * kb, kb);
-    cudaFree(d_off); cudaFree(d_k); cudaFree(d_v);
     return FQ_OK;
 }
 
@@ -1321,8 +1332,9 @@ extern "C" int fq_run_lookup(fq_run* r, const fq_key* keys, size_t n, double* am
     pack_keys(keys, n, kb, kbuf);
     void* d_k = nullptr;
     double* d_a = nullptr;
-    CK(cudaMalloc(&d_k, kb * n));
-    CK(cudaMalloc((void**)&d_a, sizeof(double) * n));
+    CallBufs bufs;  // released on every return
+    CK(bufs.get(&d_k, kb * n));
+    CK(bufs.get(&d_a, sizeof(double) * n));
     cudaError_t e = cudaMemcpy(d_k, kbuf.data(), kb * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         r->ks->lookup(r->d_self, d_k, n, d_a, r->stream);
@@ -1330,8 +1342,6 @@ extern "C" int fq_run_lookup(fq_run* r, const fq_key* keys, size_t n, double* am
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
     if (e == cudaSuccess) e = cudaMemcpy(amps, d_a, sizeof(double) * n, cudaMemcpyDeviceToHost);
-    cudaFree(d_k);
-    cudaFree(d_a);
     return cuda_err(e);
 }
 
@@ -1372,10 +1382,11 @@ extern "C" int fq_run_sample(fq_run* r, uint64_t seed, size_t want, fq_key* keys
         unsigned *d_off = nullptr, *d_segs = nullptr;
         void* d_k = nullptr;
         double* d_v = nullptr;
-        CK(cudaMalloc((void**)&d_off, sizeof(unsigned) * off.size()));
-        CK(cudaMalloc((void**)&d_segs, sizeof(unsigned) * segs.size()));
-        CK(cudaMalloc(&d_k, kb * tot));
-        CK(cudaMalloc((void**)&d_v, sizeof(double) * tot));
+        CallBufs bufs;  // released on every return
+        CK(bufs.get(&d_off, sizeof(unsigned) * off.size()));
+        CK(bufs.get(&d_segs, sizeof(unsigned) * segs.size()));
+        CK(bufs.get(&d_k, kb * tot));
+        CK(bufs.get(&d_v, sizeof(double) * tot));
         CK(cudaMemcpy(d_off, off.data(), sizeof(unsigned) * off.size(), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(d_segs, segs.data(), sizeof(unsigned) * segs.size(), cudaMemcpyHostToDevice));
         r->ks->gather_vec(r->vkeys[cur], r->vamps[cur], r->Cv, r->vcount[cur], d_off,
@@ -1385,7 +1396,6 @@ extern "C" int fq_run_sample(fq_run* r, uint64_t seed, size_t want, fq_key* keys
         std::vector<double> v(tot);
         CK(cudaMemcpy(kbuf.data(), d_k, kb * tot, cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(v.data(), d_v, sizeof(double) * tot, cudaMemcpyDeviceToHost));
-        cudaFree(d_off); cudaFree(d_segs); cudaFree(d_k); cudaFree(d_v);
         const size_t w = std::min(cap, tot);
         for (size_t i = 0; i < w; ++i) {
             fq_key k = {0, 0};
