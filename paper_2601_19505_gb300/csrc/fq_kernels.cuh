@@ -662,15 +662,17 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
             }
             // the table is the warp's own: only lanes of this round that hit
             // the same slot conflict.  They pass their values to the lowest
-            // of them, which adds the group's sum with a plain update.
+            // of them, which adds the group's sum with a plain update, or
+            // stores it when a lane of the group created the slot this round
+            // (its sum is still 0; nearly every spawn reaches a new address).
             const unsigned grp = __match_any_sync(0xFFFFFFFFu, q);
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, nw);
             if (q >= 0) {
                 ACC sum = (ACC)v;
                 for (unsigned o = grp & (grp - 1u); o; o &= o - 1u)
                     sum = sum + (ACC)__shfl_sync(grp, v, __ffs(o) - 1);
-                if (lane == __ffs(grp) - 1) ta[q] = ta[q] + sum;
+                if (lane == __ffs(grp) - 1) ta[q] = (bal & grp) ? sum : ta[q] + sum;
             }
-            const unsigned bal = __ballot_sync(0xFFFFFFFFu, nw);
             if (nw) tl[nl + __popc(bal & ((1u << lane) - 1u))] = (unsigned)q;
             nl += __popc(bal);
         }
