@@ -166,3 +166,45 @@ def test_capacity_overflow_rolls_back():
     st = g.stats()
     k, a = g.export()
     assert len(k) == st["len"] and np.isclose(np.abs(a).sum(), st["norm"], rtol=1e-12)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_reserve_after_overflow_continues_the_same_run(mode):
+    """A run that overflows a small capacity is rolled back to its last
+    completed step; after fq_run_reserve it continues exactly as a run
+    created large enough from the start (integer walkers: bit-exact; FP64:
+    the same addresses, amplitudes to 1e-12)."""
+    h, m = pair(*MODELS[1])
+    prm = dict(mode=mode, dt=0.001, target=2e5, seed=5)
+    small = fq().Run(h, fq().default_params(capacity_vec=4096, capacity_spawn=4096, **prm))
+    big = fq().Run(h, fq().default_params(capacity_vec=1 << 20, capacity_spawn=1 << 21, **prm))
+    small.seed_default(10.0)
+    big.seed_default(10.0)
+    grows = small.advance(600, chunk=50)
+    big.step(600)
+    assert grows >= 1
+    assert small.stats()["step"] == big.stats()["step"] == 600
+    (ks, as_), (kb, ab) = small.export(), big.export()
+    assert np.array_equal(ks, kb)
+    if mode == 0:
+        assert np.array_equal(as_, ab)
+    else:
+        assert np.allclose(as_, ab, rtol=1e-12, atol=0)
+    hs, hb = small.history(), big.history()
+    assert np.array_equal(hs["len"], hb["len"])
+    assert np.array_equal(hs["step"], hb["step"])
+
+
+def test_launch_shape_and_profile():
+    h, m = pair(*MODELS[1])
+    g = fq().Run(h, fq().default_params(dt=0.001, target=1e5, seed=3))
+    g.seed_default(10.0)
+    g.step(300)
+    g.autotune(1)
+    shp = g.shape()
+    assert shp["spawn_wpb"] in (4, 8) and shp["merge_wpb"] in (4, 8)
+    assert shp["spawn_grid"] > 0 and shp["merge_grid"] > 0 and shp["slots"] >= 64
+    before = g.stats()["step"]
+    ms = g.profile(5)
+    assert g.stats()["step"] == before + 5
+    assert ms[0] > 0 and ms[1] > 0 and ms[2] > 0
