@@ -6,26 +6,27 @@
 //            column's spawns H_ji coef_i, coef_i = -dt c_i (exact) or
 //            -dt (m_i / n_i) c_i for n_i = ceil|c_i| uniform picks (Eq.
 //            column-compression), into the bucket owning each destination.
-//   k_merge  For every bucket: put c^(n)'s segment, with the diagonal factor
-//            1 + dt (S - H_ii) applied, and every spawn to the bucket into an
-//            on-chip open-addressing table, which sums contributions per
-//            address (annihilation); apply vector compression Pi (Eq.
-//            vec-compression); compact the survivors into c^(n+1)'s
-//            segment; accumulate ||c||_1 (exactly), len and the
-//            projected-energy terms.
+//   k_merge  For every bucket: sum the spawns to the bucket per address in
+//            an on-chip open-addressing table (annihilation); give each entry
+//            of c^(n)'s segment its diagonal term 1 + dt (S - H_ii) plus the
+//            sum of its address, then the addresses only spawns reached;
+//            apply vector compression Pi (Eq. vec-compression); compact the
+//            survivors into c^(n+1)'s segment; accumulate ||c||_1 (exactly),
+//            len and the projected-energy terms.
 //   k_shift  One block per run: Eq. shift-update, a history row, the buffer
 //            flip, and the diagonal-factor table of the next step.
 //
 // Layout: the vector of a run is hash-segmented (the paper's PDVec segments,
-// Sec. 6.4, as thousands of small segments sized for one SM's shared
-// memory): segment b = top log2(B) bits of fmix64(h(address)), capacity Cv
+// Sec. 6.4, as thousands of small segments sized for one merge warp's
+// on-chip table): segment b = top log2(B) bits of fmix64(h(address)), capacity Cv
 // entries each, structure-of-arrays keys/amplitudes.  Spawn buckets use the
 // same segment map with capacity Cs.  All sizes and pointers are read from
 // device memory, so one captured CUDA graph replays any number of steps.
 //
 // GB300 executes FP64 at a small fraction of its FP32/integer rate, so the
-// kernels keep FP64 work to about one multiply per spawn and per entry (FP64
-// amplitudes) or none (FP32 amplitudes); decisions whose result is exact are
+// kernels keep FP64 work to about one multiply per spawn and one multiply
+// and add per entry (FP64 amplitudes) or none (FP32 amplitudes); decisions
+// whose result is exact are
 // taken on integer bits (fq_device.cuh), with results identical to the FP64
 // expressions they stand for.
 #pragma once
