@@ -160,15 +160,9 @@ __device__ __forceinline__ unsigned pick(uint4 w, unsigned m) {
     return (unsigned)(((unsigned long long)w.z * (unsigned long long)m) >> 32);
 }
 
-// murmur3 64-bit finaliser (Appleby): segment = top bits, table slot = low bits
-__device__ __forceinline__ uint64_t fmix64(uint64_t h) {
-    h ^= h >> 33;
-    h *= 0xFF51AFD7ED558CCDull;
-    h ^= h >> 33;
-    h *= 0xC4CEB9FE1A85EC53ull;
-    h ^= h >> 33;
-    return h;
-}
+// segment hash: multiplicative (Fibonacci) hashing, h times the 64-bit
+// golden-ratio constant; the segment is the product's top bits
+__device__ __forceinline__ uint64_t seg_mix(uint64_t h) { return h * 0x9E3779B97F4A7C15ull; }
 __device__ __forceinline__ unsigned segment_of(uint64_t mixed, int log2B) {
     return log2B ? (unsigned)(mixed >> (64 - log2B)) : 0u;
 }

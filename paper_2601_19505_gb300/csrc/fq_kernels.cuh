@@ -18,7 +18,7 @@
 //
 // Layout: the vector of a run is hash-segmented (the paper's PDVec segments,
 // Sec. 6.4, as thousands of small segments sized for one merge warp's
-// on-chip table): segment b = top log2(B) bits of fmix64(h(address)), capacity Cv
+// on-chip table): segment b = top log2(B) bits of seg_mix(h(address)), capacity Cv
 // entries each, structure-of-arrays keys/amplitudes.  Spawn buckets use the
 // same segment map with capacity Cs.  All sizes and pointers are read from
 // device memory, so one captured CUDA graph replays any number of steps.
@@ -288,7 +288,7 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     auto emit = [&](bool has, K dest, S val) {
         unsigned bk = 0, pos = 0;
         if (has) {
-            bk = segment_of(fmix64(KeyOps<K>::rng_h(dest)), log2B);
+            bk = segment_of(seg_mix(KeyOps<K>::rng_h(dest)), log2B);
             pos = atomicAdd(&sfill[bk], 1u);
             ++n_sp;
         }
@@ -527,7 +527,8 @@ __device__ __forceinline__ bool compress(typename AmpT<AMP>::ACC w, const RunDes
 __device__ __forceinline__ void merge_flush(const RunDesc* R, unsigned long long nlo,
                                             unsigned long long nhi, unsigned long long nlen,
                                             double nfp, bool full, bool over, bool range_bad,
-                                            int lane) {
+                                            unsigned long long ntheta, int lane) {
+    add128(nlo, nhi, ntheta << 52, ntheta >> 12);  // the values of magnitude theta
     warp_sum128(nlo, nhi);
     nlen = warp_sum(nlen);
     nfp = warp_sum(nfp);
@@ -554,6 +555,7 @@ struct MergeAcc {
     unsigned long long nlo, nhi, nlen;
     double nfp;
     bool full, over, range_bad;
+    unsigned long long ntheta;  // stored values of magnitude theta (a power of two)
 };
 
 // a table sum that an entry of c^(n) has taken over (no valid sum has these
@@ -602,6 +604,8 @@ __device__ __forceinline__ void merge_emit(const RunDesc* R, bool has, K key,
         } else {
             if (det) {
                 acc.nfp += fabs((double)out);
+            } else if (R->theta_pow2 && abs_dbits(out) == dbits(R->theta)) {
+                ++acc.ntheta;  // theta = 2^(nq + 52): 2^52 units, added at the flush
             } else {
                 unsigned long long lo, hi;
                 fixed_of(out, nq, lo, hi, acc.range_bad);
@@ -821,7 +825,7 @@ k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     const RunDesc* R = nullptr;
     unsigned run_lo = 0, run_hi = 0;  // segments of the current run
     unsigned err = 0, cur = 0;
-    MergeAcc acc = {0, 0, 0, 0.0, false, false, false};
+    MergeAcc acc = {0, 0, 0, 0.0, false, false, false, 0};
     // counts of buckets ahead_g and ahead2_g, loaded before they are needed
     unsigned ahead_g = 0xFFFFFFFFu, ahead2_g = 0xFFFFFFFFu;
     unsigned a1_old = 0, a1_sp = 0, a2_old = 0, a2_sp = 0;
@@ -830,8 +834,8 @@ k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
         if (g < run_lo || g >= run_hi) {  // warp-uniform
             if (R) {
                 merge_flush(R, acc.nlo, acc.nhi, acc.nlen, acc.nfp, acc.full, acc.over,
-                            acc.range_bad, lane);
-                acc = MergeAcc{0, 0, 0, 0.0, false, false, false};
+                            acc.range_bad, acc.ntheta, lane);
+                acc = MergeAcc{0, 0, 0, 0.0, false, false, false, 0};
             }
             R = runs + seg_run[g];
             run_lo = R->seg_base;
@@ -907,7 +911,7 @@ k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     }
     if (R)
         merge_flush(R, acc.nlo, acc.nhi, acc.nlen, acc.nfp, acc.full, acc.over, acc.range_bad,
-                    lane);
+                    acc.ntheta, lane);
 }
 
 // scratch tables start empty (keys EMPTY, sums 0); each use leaves them so
@@ -1042,7 +1046,7 @@ __global__ void k_seed(const RunDesc* __restrict__ R, const K* __restrict__ keys
     if (i >= n) return;
     const int cur = R->st->cur;
     const K key = keys[i];
-    const unsigned b = segment_of(fmix64(KeyOps<K>::rng_h(key)), R->log2B);
+    const unsigned b = segment_of(seg_mix(KeyOps<K>::rng_h(key)), R->log2B);
     const unsigned pos = atomicAdd(&R->vcount[cur][b], 1u);
     if (pos < R->Cv) {
         ((K*)R->vkeys[cur])[(size_t)b * R->Cv + pos] = key;
@@ -1076,7 +1080,7 @@ __global__ void k_lookup(const RunDesc* __restrict__ R, const K* __restrict__ q,
     if (i >= n) return;
     const int cur = R->st->cur;
     const K key = q[i];
-    const unsigned b = segment_of(fmix64(KeyOps<K>::rng_h(key)), R->log2B);
+    const unsigned b = segment_of(seg_mix(KeyOps<K>::rng_h(key)), R->log2B);
     const unsigned c = min(R->vcount[cur][b], R->Cv);
     const K* vk = (const K*)R->vkeys[cur] + (size_t)b * R->Cv;
     const A* va = (const A*)R->vamps[cur] + (size_t)b * R->Cv;
@@ -1134,7 +1138,7 @@ __global__ void k_ref_terms(ModelParams mp, const K* __restrict__ refs, const do
     tkeys[o] = key;
     th[o] = y[r] * MD::diagonal(mp, key);
     tv[o] = y[r];
-    tseg[o] = segment_of(fmix64(KeyOps<K>::rng_h(key)), log2B);
+    tseg[o] = segment_of(seg_mix(KeyOps<K>::rng_h(key)), log2B);
     ++o;
     for (unsigned k = 0; k < m; ++k, ++o) {
         double hv;
@@ -1142,7 +1146,7 @@ __global__ void k_ref_terms(ModelParams mp, const K* __restrict__ refs, const do
         tkeys[o] = d;
         th[o] = y[r] * hv;
         tv[o] = 0.0;
-        tseg[o] = segment_of(fmix64(KeyOps<K>::rng_h(d)), log2B);
+        tseg[o] = segment_of(seg_mix(KeyOps<K>::rng_h(d)), log2B);
     }
 }
 
