@@ -160,9 +160,25 @@ __device__ __forceinline__ unsigned pick(uint4 w, unsigned m) {
     return (unsigned)(((unsigned long long)w.z * (unsigned long long)m) >> 32);
 }
 
-// segment hash: multiplicative (Fibonacci) hashing, h times the 64-bit
-// golden-ratio constant; the segment is the product's top bits
-__device__ __forceinline__ uint64_t seg_mix(uint64_t h) { return h * 0x9E3779B97F4A7C15ull; }
+// segment hash; the segment is the top bits.  64-bit addresses: one
+// multiply by an odd constant (multiplicative hashing), unrelated to the
+// golden-ratio constant of the merge table's slot hash (with related
+// constants, small addresses that share a segment would also share a few
+// table slots).  128-bit addresses (h already folds the high word through
+// splitmix64): the murmur3 64-bit finaliser (Appleby), which measured faster
+// for them.
+__device__ __forceinline__ uint64_t fmix64(uint64_t h) {
+    h ^= h >> 33;
+    h *= 0xFF51AFD7ED558CCDull;
+    h ^= h >> 33;
+    h *= 0xC4CEB9FE1A85EC53ull;
+    h ^= h >> 33;
+    return h;
+}
+template <class K> __device__ __forceinline__ uint64_t seg_mix(uint64_t h) {
+    if constexpr (sizeof(K) == 8) return h * 0xD6E8FEB86659FD93ull;
+    else return fmix64(h);
+}
 __device__ __forceinline__ unsigned segment_of(uint64_t mixed, int log2B) {
     return log2B ? (unsigned)(mixed >> (64 - log2B)) : 0u;
 }

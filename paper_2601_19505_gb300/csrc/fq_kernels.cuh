@@ -288,7 +288,7 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     auto emit = [&](bool has, K dest, S val) {
         unsigned bk = 0, pos = 0;
         if (has) {
-            bk = segment_of(seg_mix(KeyOps<K>::rng_h(dest)), log2B);
+            bk = segment_of(seg_mix<K>(KeyOps<K>::rng_h(dest)), log2B);
             pos = atomicAdd(&sfill[bk], 1u);
             ++n_sp;
         }
@@ -1046,7 +1046,7 @@ __global__ void k_seed(const RunDesc* __restrict__ R, const K* __restrict__ keys
     if (i >= n) return;
     const int cur = R->st->cur;
     const K key = keys[i];
-    const unsigned b = segment_of(seg_mix(KeyOps<K>::rng_h(key)), R->log2B);
+    const unsigned b = segment_of(seg_mix<K>(KeyOps<K>::rng_h(key)), R->log2B);
     const unsigned pos = atomicAdd(&R->vcount[cur][b], 1u);
     if (pos < R->Cv) {
         ((K*)R->vkeys[cur])[(size_t)b * R->Cv + pos] = key;
@@ -1080,7 +1080,7 @@ __global__ void k_lookup(const RunDesc* __restrict__ R, const K* __restrict__ q,
     if (i >= n) return;
     const int cur = R->st->cur;
     const K key = q[i];
-    const unsigned b = segment_of(seg_mix(KeyOps<K>::rng_h(key)), R->log2B);
+    const unsigned b = segment_of(seg_mix<K>(KeyOps<K>::rng_h(key)), R->log2B);
     const unsigned c = min(R->vcount[cur][b], R->Cv);
     const K* vk = (const K*)R->vkeys[cur] + (size_t)b * R->Cv;
     const A* va = (const A*)R->vamps[cur] + (size_t)b * R->Cv;
@@ -1138,7 +1138,7 @@ __global__ void k_ref_terms(ModelParams mp, const K* __restrict__ refs, const do
     tkeys[o] = key;
     th[o] = y[r] * MD::diagonal(mp, key);
     tv[o] = y[r];
-    tseg[o] = segment_of(seg_mix(KeyOps<K>::rng_h(key)), log2B);
+    tseg[o] = segment_of(seg_mix<K>(KeyOps<K>::rng_h(key)), log2B);
     ++o;
     for (unsigned k = 0; k < m; ++k, ++o) {
         double hv;
@@ -1146,7 +1146,7 @@ __global__ void k_ref_terms(ModelParams mp, const K* __restrict__ refs, const do
         tkeys[o] = d;
         th[o] = y[r] * hv;
         tv[o] = 0.0;
-        tseg[o] = segment_of(seg_mix(KeyOps<K>::rng_h(d)), log2B);
+        tseg[o] = segment_of(seg_mix<K>(KeyOps<K>::rng_h(d)), log2B);
     }
 }
 
