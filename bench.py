@@ -548,6 +548,55 @@ def equal_error_arm(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# c3 (momentum space, sign problem): FP32 against FP64 amplitudes at the step
+# where the population first reaches N_t.  The overshoot that follows (about
+# ten times N_t) leaves no equilibrated window, so this compares throughput
+# on the same state size, not error bars.
+
+def c3_precision_arm(args):
+    import torch
+
+    import paper_2601_19505_gb300 as fq
+
+    torch.cuda.set_device(0)
+    cfg = W.CONFIGS["c3"]
+    out = {}
+    for mode in ("REAL32", "REAL64"):
+        h = fq.Hamiltonian(cfg["kind"], cfg["Lx"], cfg["Ly"], cfg["N"], cfg["t"], cfg["u"])
+        p = fq.default_params(mode=MODE_CODE[mode], dt=cfg["dt"], target=cfg["target"],
+                              seed=cfg["seed"])
+        run = fq.Run(h, p)
+        run.seed_default(W.START_WEIGHT)
+        st = run.stats()
+        while st["norm"] < cfg["target"] and st["step"] < 1000:
+            run.advance(2, chunk=2)
+            st = run.stats()
+        run.reserve(int(5e8), int(1e9))  # the timed steps keep growing ~25 % each
+        before = run.stats()
+        n = min(args.steps, 3)
+        ms = run.profile(n)
+        hist = run.history()
+        units = float(hist["len"][-n:].sum())
+        t = (ms[0] + ms[1] + ms[2]) * 1e-3 * n
+        out[mode] = {"configs_per_s": units / t, "ms_per_step": 1e3 * t / n,
+                     "kernel_ms": {"spawn": ms[0], "merge": ms[1], "shift": ms[2]},
+                     "step": before["step"], "len": before["len"], "norm": before["norm"]}
+        run.close()
+        del run
+        torch.cuda.empty_cache()
+    line = {"metric": METRIC + " (c3, FP32 vs FP64 amplitudes at N = N_t)",
+            "value": out["REAL32"]["configs_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": min(args.steps, 3), "warmup": 0, "ms_per_step": out["REAL32"]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": describe(cfg, "c3") + "; timed once the one-norm first "
+                                   "reaches N_t, kernel by kernel (CUDA events)"},
+            "precision": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -561,6 +610,9 @@ def main():
     ap.add_argument("--equal-error", action="store_true",
                     help="the c4 comparison: 64 runs as one FP32 batch against the same runs "
                          "one after another in FP64, at equal projected-energy error")
+    ap.add_argument("--c3-precision", action="store_true",
+                    help="c3: FP32 against FP64 amplitudes where the population first "
+                         "reaches its target")
     ap.add_argument("--mode", choices=sorted(MODE_CODE), default=None,
                     help="override the workload's amplitude mode (exploration only)")
     args = ap.parse_args()
@@ -573,6 +625,8 @@ def main():
         return reference_arm(args, cfg, args.config)
     if args.equal_error:
         return equal_error_arm(args)
+    if args.c3_precision:
+        return c3_precision_arm(args)
     return gpu_arm(args, cfg, args.config)
 
 
