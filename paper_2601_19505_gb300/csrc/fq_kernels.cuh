@@ -252,15 +252,14 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
         warp_copy_async(in_amp + b * CH, va0 + e0, cn * (unsigned)sizeof(A), lane);
         cp_async_commit();
     };
-    // attempt a of a source (key, coefficient cf, mm = m and flags): the
-    // destination and value; false when an integer spawn rounds to nothing
-    auto make = [&](K key, CO cf, unsigned mm, unsigned a, K& dest, S& val) -> bool {
+    // attempt a of a source (key, its column data col, coefficient cf, mm =
+    // m and flags): the destination and value; false when an integer spawn
+    // rounds to nothing
+    auto make_col = [&](K key, const Col& col, CO cf, unsigned mm, unsigned a, K& dest,
+                        S& val) -> bool {
         const ModelParams& mp = R->mp;
         const unsigned m = mm & 0x3FFFFFFFu;
         const bool ex = (AMP != FQ_AMP_INT) && (mm >> 31);
-        Col col;
-        if constexpr (KIND != FQ_KIND_MOM_1D) col.n_occ = (int)(m / (unsigned)MD::Z);
-        else MD::num_offdiag(mp, key, col);
         uint4 w = make_uint4(0, 0, 0, 0);
         unsigned kk = a;
         if (!ex) {
@@ -283,6 +282,14 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
         }
         return true;
     };
+    // the same, recomputing the column data from the address
+    auto make = [&](K key, CO cf, unsigned mm, unsigned a, K& dest, S& val) -> bool {
+        Col col;
+        if constexpr (KIND != FQ_KIND_MOM_1D) col.n_occ = (int)((mm & 0x3FFFFFFFu) / (unsigned)MD::Z);
+        else MD::num_offdiag(R->mp, key, col);
+        return make_col(key, col, cf, mm, a, dest, val);
+    };
+
     // reserve a bucket slot for this lane's spawn (if any) and store the
     // previous one, whose slot has arrived meanwhile
     auto emit = [&](bool has, K dest, S val) {
@@ -346,10 +353,10 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
             unsigned cnt = 0, mm = 0;
             CO cf = (CO)0;
             K key = KeyOps<K>::empty();
+            Col col;
             if (i < cn) {
                 key = wkey[i];
                 const CO c = (CO)wamp[i];
-                Col col;
                 const unsigned m = MD::num_offdiag(mp, key, col);
                 unsigned fl, ce;
                 floor_ceil_abs(c, fl, ce);
@@ -392,7 +399,7 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
             xoff += __shfl_sync(0xFFFFFFFFu, incl, 31);
             K dest = KeyOps<K>::empty();
             S val = (S)0;
-            const bool has = cnt >= 1u && make(key, cf, mm, 0u, dest, val);
+            const bool has = cnt >= 1u && make_col(key, col, cf, mm, 0u, dest, val);
             emit(has, dest, val);
         }
         __syncwarp();
