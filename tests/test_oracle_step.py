@@ -230,3 +230,14 @@ def test_integer_walker_run_matches_exact_energy():
     assert np.all(h["exact_steps"] == 0)
     assert abs(proj["ratio"] - e0) < 2 * proj["err"]
     assert abs(shift["mean"] - e0) < 2 * shift["err"]
+
+
+def test_momentum_run_matches_exact_energy():
+    """Momentum space (Sec. 6.3), 6 modes, 6 bosons, u = 4, default parameters:
+    4000 steps from the condensate, blocked estimates within 2 sigma of the
+    lowest eigenvalue of the same momentum sector."""
+    m = O.Model(O.MOM_1D, 6, 1, 6, 1.0, 4.0)
+    e0 = ED.lowest(m, 1)[0]
+    shift, proj, h = _run_energy(m, O.default_params(), 4000, 1000)
+    assert abs(proj["ratio"] - e0) < 2 * proj["err"], (proj, e0)
+    assert abs(shift["mean"] - e0) < 2 * shift["err"], (shift, e0)
