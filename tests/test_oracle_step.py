@@ -241,3 +241,14 @@ def test_momentum_run_matches_exact_energy():
     shift, proj, h = _run_energy(m, O.default_params(), 4000, 1000)
     assert abs(proj["ratio"] - e0) < 2 * proj["err"], (proj, e0)
     assert abs(shift["mean"] - e0) < 2 * shift["err"], (shift, e0)
+
+
+def test_two_dimensional_run_matches_exact_energy():
+    """2D 3x3 periodic lattice, 4 bosons, u = 3, default parameters: 4000
+    steps from near-uniform filling, blocked estimates within 2 sigma of
+    exact diagonalisation."""
+    m = O.Model(O.REAL_2D, 3, 3, 4, 1.0, 3.0)
+    e0 = ED.lowest(m, 1)[0]
+    shift, proj, h = _run_energy(m, O.default_params(), 4000, 1000)
+    assert abs(proj["ratio"] - e0) < 2 * proj["err"], (proj, e0)
+    assert abs(shift["mean"] - e0) < 2 * shift["err"], (shift, e0)
