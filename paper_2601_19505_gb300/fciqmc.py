@@ -24,6 +24,7 @@ STATS_DTYPE = np.dtype([("step", "<i8"), ("len", "<i8"), ("exact_steps", "<i8"),
 
 
 class FqError(RuntimeError):
+    """A negative status code of the C ABI (FQ_ERR_*), with the call that returned it."""
     def __init__(self, code: int, what: str):
         self.code = code
         msg = L.load().fq_strerror(code).decode()
@@ -49,10 +50,12 @@ def _ptr(a: np.ndarray):
 
 
 def version() -> str:
+    """fq_version: the library version string."""
     return L.load().fq_version().decode()
 
 
 def keys_from_ints(keys) -> np.ndarray:
+    """Python integers (addresses up to 128 bits) as an fq_key array (lo, hi)."""
     out = np.zeros(len(keys), dtype=KEY_DTYPE)
     for i, k in enumerate(keys):
         k = int(k)
@@ -61,6 +64,7 @@ def keys_from_ints(keys) -> np.ndarray:
 
 
 def keys_to_ints(keys: np.ndarray):
+    """An fq_key array as Python integers."""
     return [int(k["lo"]) | (int(k["hi"]) << 64) for k in keys]
 
 
@@ -105,22 +109,26 @@ class Hamiltonian:
             self.h = None
 
     def dimension(self) -> float:
+        """fq_ham_dimension: the Fock-space dimension C(N + M - 1, N), as a float."""
         d = C.c_double()
         _check(self._lib.fq_ham_dimension(self.h, C.byref(d)), "fq_ham_dimension")
         return d.value
 
     def starting_address(self) -> int:
+        """fq_ham_starting_address: near-uniform filling (real space) or the k = 0 condensate."""
         k = L.FqKey()
         _check(self._lib.fq_ham_starting_address(self.h, C.byref(k)), "fq_ham_starting_address")
         return k.lo | (k.hi << 64)
 
     def encode(self, occ) -> int:
+        """fq_encode: occupation numbers of the M modes to an address (an int)."""
         o = np.ascontiguousarray(occ, dtype=np.uint8)
         k = L.FqKey()
         _check(self._lib.fq_encode(self.h, _ptr(o), C.byref(k)), "fq_encode")
         return k.lo | (k.hi << 64)
 
     def decode(self, key) -> np.ndarray:
+        """fq_decode: an address to the occupation numbers of the M modes."""
         o = np.zeros(self.M, dtype=np.uint8)
         k = int(key)
         _check(self._lib.fq_decode(self.h, L.FqKey(k & 0xFFFFFFFFFFFFFFFF, k >> 64), _ptr(o)),
@@ -153,6 +161,7 @@ class _TorchAllocator:
         self.struct = L.FqAllocator(None, self._alloc, self._free)
 
     def alloc(self, ctx, nbytes, stream):
+        """Device allocation for the C library, from the caching allocator (None on failure)."""
         try:
             return self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device,
                                                            int(stream or 0))
@@ -160,6 +169,7 @@ class _TorchAllocator:
             return None
 
     def free(self, ctx, ptr, nbytes, stream):
+        """Release an allocation made by alloc."""
         self.torch.cuda.caching_allocator_delete(int(ptr))
 
 
@@ -187,6 +197,7 @@ class Run:
         self.r = r
 
     def close(self):
+        """Release the handle and its device memory (also done on garbage collection)."""
         if getattr(self, "r", None):
             self._lib.fq_run_destroy(self.r)
             self.r = None
@@ -201,52 +212,64 @@ class Run:
         self.close()
 
     def seed(self, keys, amps, shift: float, step: int = 0):
+        """fq_run_seed: replace the vector by (keys, amps); set the shift and the step counter."""
         k = _as_keys(keys)
         a = np.ascontiguousarray(amps, dtype=np.float64)
         _check(self._lib.fq_run_seed(self.r, _ptr(k), _ptr(a), len(a), float(shift), int(step)),
                "fq_run_seed")
 
     def seed_default(self, weight: float = 10.0):
+        """fq_run_seed_default: `weight` walkers on the starting address, shift = its diagonal."""
         _check(self._lib.fq_run_seed_default(self.r, float(weight)), "fq_run_seed_default")
 
     def set_reference(self, keys, y):
+        """fq_run_set_reference: the projected-energy reference y (addresses, coefficients)."""
         k = _as_keys(keys)
         a = np.ascontiguousarray(y, dtype=np.float64)
         _check(self._lib.fq_run_set_reference(self.r, _ptr(k), _ptr(a), len(a)),
                "fq_run_set_reference")
 
     def set_dt(self, dt: float):
+        """fq_run_set_dt: the time step of the following steps."""
         _check(self._lib.fq_run_set_dt(self.r, float(dt)), "fq_run_set_dt")
 
     def set_shift(self, s: float):
+        """fq_run_set_shift: the current shift."""
         _check(self._lib.fq_run_set_shift(self.r, float(s)), "fq_run_set_shift")
 
     def set_target(self, t: float):
+        """fq_run_set_target: the target one-norm N_t."""
         _check(self._lib.fq_run_set_target(self.r, float(t)), "fq_run_set_target")
 
     def step(self, n: int = 1):
+        """Enqueue n steps (asynchronous; errors surface at the next synchronising call)."""
         _check(self._lib.fq_run_step(self.r, int(n)), "fq_run_step")
 
     def sync(self) -> int:
+        """Wait for queued steps; the status code (0, or a negative FQ_ERR_* after a rollback)."""
         return self._lib.fq_run_sync(self.r)
 
     def error_bits(self) -> int:
+        """fq_run_error_bits: the device-side cause of the last reported error."""
         b = C.c_uint()
         _check(self._lib.fq_run_error_bits(self.r, C.byref(b)), "fq_run_error_bits")
         return b.value
 
     def stats(self) -> dict:
+        """fq_run_stats: the row of the last completed step as a dict (synchronises)."""
         s = L.FqStats()
         self._chk(self._lib.fq_run_stats(self.r, C.byref(s)), "fq_run_stats")
         return {f: getattr(s, f) for f, _ in L.FqStats._fields_}
 
     def history(self, cap: int = 1 << 16) -> np.ndarray:
+        """fq_run_history: the rows recorded since the last call (STATS_DTYPE array)."""
         out = np.zeros(cap, dtype=STATS_DTYPE)
         n = C.c_size_t()
         self._chk(self._lib.fq_run_history(self.r, _ptr(out), cap, C.byref(n)), "fq_run_history")
         return out[: n.value].copy()
 
     def export(self):
+        """fq_run_export: (keys, amplitudes) of the vector, sorted by address."""
         n = C.c_size_t()
         self._chk(self._lib.fq_run_export(self.r, None, None, 0, C.byref(n)), "fq_run_export")
         cap = n.value
@@ -274,6 +297,7 @@ class Run:
         return k[:m].copy(), a[:m].copy()
 
     def spawns(self, cap: int | None = None):
+        """fq_run_spawns: (destinations, values) of the next step's spawns; the run does not change."""
         n = C.c_size_t()
         if cap is None:
             cap = 1 << 22
@@ -285,13 +309,16 @@ class Run:
         return d[: n.value].copy(), v[: n.value].copy()
 
     def autotune(self, steps: int = 3):
+        """Time the launch shapes on real steps and keep the fastest (the run advances)."""
         _check(self._lib.fq_run_autotune(self.r, int(steps)), "fq_run_autotune")
 
     def reserve(self, capacity_vec: int, capacity_spawn: int):
+        """fq_run_reserve: grow the vector and spawn capacities, keeping the vector."""
         _check(self._lib.fq_run_reserve(self.r, int(capacity_vec), int(capacity_spawn)),
                "fq_run_reserve")
 
     def capacity(self):
+        """fq_run_capacity: (vector entries, spawns per step) the run can hold."""
         v, s = C.c_size_t(), C.c_size_t()
         _check(self._lib.fq_run_capacity(self.r, C.byref(v), C.byref(s)), "fq_run_capacity")
         return v.value, s.value
@@ -344,6 +371,7 @@ class Batch:
         self.b = b
 
     def close(self):
+        """Release the handle and its device memory (also done on garbage collection)."""
         if getattr(self, "b", None):
             self._lib.fq_batch_destroy(self.b)
             self.b = None
@@ -352,10 +380,13 @@ class Batch:
         self.close()
 
     def step(self, n: int = 1):
+        """Enqueue n steps (asynchronous; errors surface at the next synchronising call)."""
         _check(self._lib.fq_batch_step(self.b, int(n)), "fq_batch_step")
 
     def sync(self):
+        """fq_batch_sync: wait and report the first error of the batch's runs."""
         _check(self._lib.fq_batch_sync(self.b), "fq_batch_sync")
 
     def autotune(self, steps: int = 3):
+        """Time the launch shapes on real steps and keep the fastest (the run advances)."""
         _check(self._lib.fq_batch_autotune(self.b, int(steps)), "fq_batch_autotune")
