@@ -1,11 +1,12 @@
 #!/usr/bin/env python
 """FCIQMC configurations updated per second on GB300.
 
-Workload (default ``c2``): 1D periodic real-space Bose-Hubbard model, M = N =
-20, t = 1, U = 2 (39-bit addresses), FP64 amplitudes, threshold 1, target
-N_t = 1e7 walkers, dt = 1e-3, started from N_w = 10 on uniform filling.  The
-first 25 % of the configuration's 10k steps are equilibration (untimed, as the
-paper discards equilibration); then W warm-up steps and K timed steps.
+Headline workload (default): c5 in the paper's FP64 arithmetic -- 2D periodic
+8 x 8 real-space Bose-Hubbard model, N = 64, t = 1, U = 8 (127-bit addresses),
+FP64 amplitudes, threshold 1, target N_t = 5e8 walkers, dt = 2e-4, started
+from N_w = 10 on uniform filling.  The first 25 % of the configuration's 2000
+steps are equilibration (untimed, as the paper discards equilibration); then
+the autotuner, W warm-up steps and K timed steps.
 
 value   = sum over timed steps of len (occupied configurations updated) /
           device time of the K steps (CUDA events on the run's stream,
@@ -18,6 +19,11 @@ roofline= the dominant kernel's algorithmic bytes per launch / its mean
           the timed region), against the measured HBM copy bandwidth.
 cpu_baseline = the CPU oracle, single thread, on a bounded sample of the
           equilibrated vector (rank 0, N = 1 only).
+
+At N = 1 the same JSON line also carries, under "more", the other measured
+forms: c5 as configured (FP32 amplitudes), c2 (1D, FP64), and the c4
+equal-error comparison (64 runs as one FP32 batch, as one FP64 batch, and
+one after another in FP64).  --config/--mode pick another workload alone.
 
 --impl reference runs the CPU oracle instead (the paper ships no GPU code):
 each step is one oracle step on a bounded sample of the same workload.
@@ -49,7 +55,7 @@ UNIT = "configs/s"
 MODE_CODE = {"INT": 0, "REAL64": 1, "REAL32": 2, "DETERMINISTIC": 3}
 DTYPE = {"INT": "int64", "REAL64": "f64", "REAL32": "f32", "DETERMINISTIC": "f64"}
 # bytes fq_run_stats copies back per call: the error word and the run state
-STATS_D2H_BYTES = 4 + 176  # the error word, then the 176-byte run state
+STATS_D2H_BYTES = 4 + 192  # the error word, then the 192-byte run state
 KERNEL_FILES = ["fq_kernels.cuh", "fq_device.cuh", "fq_shared.h"]
 
 
@@ -303,14 +309,22 @@ def reference_arm(args, cfg, name):
 # ---------------------------------------------------------------------------
 # GPU arm
 
-def gpu_arm(args, cfg, name):
+def release_device_memory():
+    import gc
+
+    import torch
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
+def gpu_arm(args, cfg, name, dist, with_cpu=True):
+    """Measure one workload; the JSON object of the line (rank 0) or None."""
     import torch
 
     import paper_2601_19505_gb300 as fq
 
     rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dist = Dist(world, "nccl")
     h = fq.Hamiltonian(cfg["kind"], cfg["Lx"], cfg["Ly"], cfg["N"], cfg["t"], cfg["u"])
     p = fq.default_params(mode=MODE_CODE[cfg["mode"]], dt=cfg["dt"], target=cfg["target"],
                           seed=cfg["seed"], run_id=rank)
@@ -319,9 +333,8 @@ def gpu_arm(args, cfg, name):
     equil = args.equil if args.equil is not None else cfg["steps"] // 4
     done = 0
     while done < equil:
-        k = min(500, equil - done)
-        run.step(k)
-        run.stats()
+        k = min(250, equil - done)
+        run.advance(k, chunk=k)  # grows the capacities if a step overflows them
         done += k
     tune_steps = 0
     if not args.no_autotune:
@@ -377,19 +390,23 @@ def gpu_arm(args, cfg, name):
         e2e_units += run.stats()["len"]
     e2e_t = time.perf_counter() - t0
     e2e_value, _ = aggregate(dist, e2e_t, float(e2e_units))
+    paths = run.merge_paths()
 
     out = None
     if rank == 0:
         cpu = None
-        if world == 1 and not args.no_cpu_baseline:
-            keys, amps = run.export()
+        if world == 1 and with_cpu and not args.no_cpu_baseline:
+            # a bounded random sample of whole segments of the equilibrated
+            # vector (exporting the whole vector would take minutes at 5e8)
+            keys, amps = run.sample(400000, seed=1)
             kint = [int(k["lo"]) | (int(k["hi"]) << 64) for k in keys] if kb == 16 else \
                 keys["lo"].astype(object).tolist()
             st = run.stats()
             rate, n, tsec = oracle_rate(cfg, kint, amps, st["shift"], st["step"])
             cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": "one single-threaded oracle step on %d entries drawn at random from "
-                             "the equilibrated GPU vector (len %d), %.1f s" % (n, len(keys), tsec)}
+                             "whole segments of the equilibrated GPU vector (len %d), %.1f s"
+                             % (n, st["len"], tsec)}
         L_mean = float(hist["len"].mean())
         S_mean = float(hist["n_spawns"].mean())
         ws = 2 * L_mean * (kb + ab) + 2 * S_mean * (kb + sb)
@@ -405,7 +422,9 @@ def gpu_arm(args, cfg, name):
                        "graph_replay": True,
                        "l2": "working set per step %.2f GB > 129 MB L2; no flush" % (ws / 1e9),
                        "parallelism": "replicas x%d" % world,
-                       "launch_shape": run.shape()},
+                       "launch_shape": run.shape(),
+                       "annihilation": "hash",
+                       "merge_buckets_onchip_scratch": list(paths)},
             "roofline": {"bound": "hbm", "kernel": "k_" + dom, "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
@@ -413,22 +432,34 @@ def gpu_arm(args, cfg, name):
                          "traffic": traffic,
                          "algorithmic_bytes_per_launch": alg[dom],
                          "kernel_ms": kms,
-                         "kernel_gbs": {k: alg[k] / (kms[k] * 1e-3) / 1e9 for k in alg}},
+                         "kernel_gbs": {k: alg[k] / (kms[k] * 1e-3) / 1e9 for k in alg},
+                         "kernel_frac": {k: alg[k] / (kms[k] * 1e-3) / 1e9 / peak for k in alg}},
             "cpu_baseline": cpu,
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8,
                     "d2h_bytes_per_step": STATS_D2H_BYTES, "steps": ne2e},
             "gpu_launches": 3 * args.steps,
         }
-        print(json.dumps(out), flush=True)
     run.close()
-    dist.close()
-    return 0
+    del run
+    release_device_memory()
+    return out
+
+
+def brief(line):
+    """The figures of a measured workload that the headline line nests."""
+    r = line["roofline"]
+    return {"workload": line["config"]["workload"], "value": line["value"], "unit": line["unit"],
+            "dtype": line["dtype"], "ms_per_step": line["ms_per_step"],
+            "len_mean": line["config"]["len_mean"], "spawns_mean": line["config"]["spawns_mean"],
+            "kernel_ms": r["kernel_ms"], "kernel_gbs": r["kernel_gbs"],
+            "kernel_frac": r["kernel_frac"], "dominant": r["kernel"], "frac": r["frac"],
+            "clocks": line.get("clocks")}
 
 
 # ---------------------------------------------------------------------------
-# Equal-error comparison: the 64 runs of c4 stepped as one FP32 batch against
-# the same 64 runs stepped one after another in plain FP64
+# Equal-error comparison: the 64 runs of c4 stepped as one FP32 batch, as one
+# FP64 batch, and one after another in plain FP64
 
 def equal_error_arm(args):
     import torch
@@ -436,7 +467,6 @@ def equal_error_arm(args):
     import paper_2601_19505_gb300 as fq
     from paper_2601_19505_gb300 import analysis as A
 
-    torch.cuda.set_device(0)
     cfgs = W.batch_configs(64, seed=1)
     steps = cfgs[0]["steps"]
     equil = steps // 4
@@ -467,32 +497,33 @@ def equal_error_arm(args):
         return (e["ratio"], e["err"], float(hist["len"].sum()), sh["mean"], sh["err"],
                 float(np.mean(hist["vproj"])), float(np.mean(hist["len"])))
 
-    # FP32 amplitudes, all 64 runs in one launch per kernel per step
-    made = [make(c, "REAL32") for c in cfgs]
-    runs32 = [r for _, r in made]
-    batch = fq.Batch(runs32)
-    batch.step(equil)
-    try:
+    def batched(mode):
+        made = [make(c, mode) for c in cfgs]
+        runs = [r for _, r in made]
+        batch = fq.Batch(runs)
+        batch.step(equil)
+        try:
+            batch.sync()
+        except fq.FqError:
+            bad = [(c["run_id"], c["Lx"], c["target"], r.error_bits(), r.capacity())
+                   for c, r in zip(cfgs, runs) if r.error_bits()]
+            raise RuntimeError("batched %s runs failed: %s" % (mode, bad))
+        if not args.no_autotune:
+            batch.autotune(2)
         batch.sync()
-    except fq.FqError:
-        bad = [(c["run_id"], c["Lx"], c["target"], r.error_bits(), r.capacity())
-               for c, r in zip(cfgs, runs32) if r.error_bits()]
-        raise RuntimeError("batched FP32 runs failed: %s" % bad)
-    tune = 0
-    if not args.no_autotune:
-        batch.autotune(2)
-        tune = 1
-    batch.sync()
-    for r in runs32:
-        r.history()
-    t32 = timed_steps(batch.step, runs32[0].stream, timed)
-    if batch.sync():
-        raise RuntimeError("batched FP32 runs failed")
-    est32 = [estimates(r.history()) for r in runs32]
-    batch.close()
-    for r in runs32:
-        r.close()
+        for r in runs:
+            r.history()
+        t = timed_steps(batch.step, runs[0].stream, timed)
+        batch.sync()
+        est = [estimates(r.history()) for r in runs]
+        batch.close()
+        for r in runs:
+            r.close()
+        release_device_memory()
+        return t, est
 
+    t32, est32 = batched("REAL32")
+    t64b, est64b = batched("REAL64")
     # plain FP64, one run after another
     t64, est64 = 0.0, []
     for c in cfgs:
@@ -505,47 +536,47 @@ def equal_error_arm(args):
             raise RuntimeError("FP64 run %d failed" % c["run_id"])
         est64.append(estimates(r.history()))
         r.close()
+    release_device_memory()
+
+    def pick(a, b):
+        # the projected energy where both forms give a finite estimate with an
+        # error bar, else the shift estimator
+        fin = all(np.isfinite(v) and v != 0.0 for v in (a[0], a[1], b[0], b[1]))
+        return (a[0], a[1], b[0], b[1], "projected") if fin else (a[3], a[4], b[3], b[4], "shift")
+
+    def compare(ta, ea, tb, eb):
+        """a against b at equal error: b's time over the time a needs for b's error bars."""
+        use = [pick(x, y) for x, y in zip(ea, eb)]
+        vr = np.array([(u[1] / u[3]) ** 2 for u in use])
+        agree = sum(1 for u in use if abs(u[0] - u[2]) <= 2.0 * math.hypot(u[1], u[3]))
+        return use, {"median_var_ratio": float(np.median(vr)), "max_var_ratio": float(vr.max()),
+                     "speedup_to_equal_error_median": tb / (ta * float(np.median(vr))),
+                     "speedup_to_equal_error_worst": tb / (ta * float(vr.max())),
+                     "energies_agree_2sigma": agree, "runs": len(use)}
 
     u32 = sum(e[2] for e in est32)
+    u64b = sum(e[2] for e in est64b)
     u64 = sum(e[2] for e in est64)
-    # the projected energy where both forms give a finite estimate with an
-    # error bar, else the shift estimator
-    use = []
-    for a, b in zip(est32, est64):
-        fin = all(np.isfinite(v) and v != 0.0 for v in (a[0], a[1], b[0], b[1]))
-        use.append((a[0], a[1], b[0], b[1], "projected") if fin else (a[3], a[4], b[3], b[4], "shift"))
-    var_ratio = np.array([(u[1] / u[3]) ** 2 for u in use])
-    agree = sum(1 for u in use if abs(u[0] - u[2]) <= 2.0 * math.hypot(u[1], u[3]))
-    # time for every run to reach the FP64 runs' error bars: the batch runs
-    # until its worst (or median) run's variance matches
-    speed_med = t64 / (t32 * float(np.median(var_ratio)))
-    speed_worst = t64 / (t32 * float(var_ratio.max()))
-    line = {"metric": METRIC + " (batched FP32 vs sequential FP64 at equal error)",
-            "value": u32 / t32, "unit": UNIT, "n_gpus": 1, "steps": timed, "warmup": equil,
-            "ms_per_step": 1e3 * t32 / timed, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "c4: 64 periodic 1D real-space Bose-Hubbard runs, M = N ~ "
-                                   "U{10..30}, U/t ~ U[1, 10], N_t log-uniform in [1e4, 1e6] "
-                                   "(default_rng(1)), dt = 1e-3, 5000 steps (first 25 % "
-                                   "untimed), 10 walkers on uniform filling",
-                       "autotuned": bool(tune)},
-            "equal_error": {
-                "fp32_batch": {"seconds": t32, "configs_per_s": u32 / t32},
-                "fp64_sequential": {"seconds": t64, "configs_per_s": u64 / t64},
-                "runs": len(cfgs),
-                "energies_agree_2sigma": agree,
-                "median_var_ratio_fp32_over_fp64": float(np.median(var_ratio)),
-                "max_var_ratio_fp32_over_fp64": float(var_ratio.max()),
-                "speedup_to_equal_error_median": speed_med,
-                "speedup_to_equal_error_worst": speed_worst,
-                "estimator_shift_runs": sum(1 for u in use if u[4] == "shift"),
-                "median_err_fp64": float(np.median([u[3] for u in use])),
-                "per_run": [{"M": c["Lx"], "U": round(c["u"], 4), "N_t": round(c["target"]),
-                             "E32": u[0], "err32": u[1], "E64": u[2], "err64": u[3], "est": u[4],
-                             "S32": a[3], "S64": b[3], "vproj64": b[5], "len64": b[6]}
-                            for c, u, a, b in zip(cfgs, use, est32, est64)]}}
-    print(json.dumps(line), flush=True)
-    return 0
+    use, total = compare(t32, est32, t64, est64)
+    _, batching = compare(t64b, est64b, t64, est64)
+    _, precision = compare(t32, est32, t64b, est64b)
+    return {
+        "workload": "c4: 64 periodic 1D real-space Bose-Hubbard runs, M = N ~ U{10..30}, "
+                    "U/t ~ U[1, 10], N_t log-uniform in [1e4, 1e6] (default_rng(1)), dt = 1e-3, "
+                    "5000 steps (first 25 % untimed), 10 walkers on uniform filling",
+        "timed_steps": timed,
+        "fp32_batch": {"seconds": t32, "configs_per_s": u32 / t32},
+        "fp64_batch": {"seconds": t64b, "configs_per_s": u64b / t64b},
+        "fp64_sequential": {"seconds": t64, "configs_per_s": u64 / t64},
+        "fp32_batch_vs_fp64_sequential": total,
+        "batching_alone_fp64_batch_vs_fp64_sequential": batching,
+        "precision_alone_fp32_batch_vs_fp64_batch": precision,
+        "estimator_shift_runs": sum(1 for u in use if u[4] == "shift"),
+        "median_err_fp64": float(np.median([u[3] for u in use])),
+        "per_run": [{"M": c["Lx"], "U": round(c["u"], 4), "N_t": round(c["target"]),
+                     "E32": u[0], "err32": u[1], "E64": u[2], "err64": u[3], "est": u[4]}
+                    for c, u in zip(cfgs, use)],
+    }
 
 
 # ---------------------------------------------------------------------------
@@ -600,34 +631,64 @@ def c3_precision_arm(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=7000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--config", choices=sorted(W.CONFIGS), default="c2")
+    ap.add_argument("--config", choices=sorted(W.CONFIGS), default="c5")
     ap.add_argument("--equil", type=int, default=None)
+    ap.add_argument("--target", type=float, default=None,
+                    help="override the workload's N_t (reduced cases for profiling)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-more", action="store_true",
+                    help="measure only the chosen workload (no nested c5-FP32, c2 and c4 lines)")
     ap.add_argument("--equal-error", action="store_true",
-                    help="the c4 comparison: 64 runs as one FP32 batch against the same runs "
-                         "one after another in FP64, at equal projected-energy error")
+                    help="only the c4 comparison: 64 runs as one FP32 batch, as one FP64 batch "
+                         "and one after another in FP64, at equal projected-energy error")
     ap.add_argument("--c3-precision", action="store_true",
                     help="c3: FP32 against FP64 amplitudes where the population first "
                          "reaches its target")
     ap.add_argument("--mode", choices=sorted(MODE_CODE), default=None,
-                    help="override the workload's amplitude mode (exploration only)")
+                    help="the amplitude mode (default: FP64 for the c5 headline, else the "
+                         "workload's own)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     cfg = dict(W.CONFIGS[args.config])
-    if args.mode:
+    headline = args.config == "c5" and args.mode is None
+    if headline:
+        cfg["mode"] = "REAL64"  # the paper's arithmetic; c5 as configured is nested below
+    elif args.mode:
         cfg["mode"] = args.mode
+    if args.target:
+        cfg["target"] = args.target
+        headline = False
     if args.impl == "reference":
         return reference_arm(args, cfg, args.config)
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
     if args.equal_error:
-        return equal_error_arm(args)
+        line = {"metric": METRIC + " (batched FP32 vs sequential FP64 at equal error)",
+                "equal_error": equal_error_arm(args)}
+        print(json.dumps(line), flush=True)
+        return 0
     if args.c3_precision:
         return c3_precision_arm(args)
-    return gpu_arm(args, cfg, args.config)
+    dist = Dist(world, "nccl")
+    out = gpu_arm(args, cfg, args.config, dist)
+    if out is not None and world == 1 and headline and not args.no_more:
+        more = {}
+        c5 = dict(W.CONFIGS["c5"])
+        more["c5_as_configured_fp32"] = brief(gpu_arm(args, c5, "c5", dist, with_cpu=False))
+        more["c2"] = brief(gpu_arm(args, dict(W.CONFIGS["c2"]), "c2", dist, with_cpu=False))
+        more["c4_equal_error"] = equal_error_arm(args)
+        out["more"] = more
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    dist.close()
+    return 0
 
 
 if __name__ == "__main__":

@@ -64,10 +64,12 @@ enum { FQ_BH_REAL_1D = 1, FQ_BH_REAL_2D = 2, FQ_BH_MOM_1D = 3 };
  * compression at all, the power iteration of Eq. fciqmc (FP64). */
 enum { FQ_MODE_INT = 0, FQ_MODE_REAL64 = 1, FQ_MODE_REAL32 = 2, FQ_MODE_DETERMINISTIC = 3 };
 
-/* Annihilation strategy.  HASH: spawns are scattered into hash-segmented
- * buckets and summed per address in an on-chip open-addressing table.  AUTO
- * picks HASH (the only one built). */
-enum { FQ_ANN_AUTO = 0, FQ_ANN_HASH = 2 };
+/* Annihilation strategy (Sec. 6.3: summing spawns to one address).  HASH:
+ * spawns are scattered into hash-segmented buckets and summed per address in
+ * an on-chip open-addressing table.  SORT: the same buckets, sorted by
+ * address and reduced by segment (not built yet: fq_run_create returns
+ * FQ_ERR_INVALID).  AUTO picks HASH. */
+enum { FQ_ANN_AUTO = 0, FQ_ANN_SORT = 1, FQ_ANN_HASH = 2 };
 
 enum {
     FQ_OK = 0,
@@ -121,6 +123,12 @@ const char *fq_strerror(int code);
  * dt = 0.01, zeta = 0.08, xi = zeta^2/4, threshold = 1, t_rel = 1,
  * target = 1000, mode REAL64, seed 1, run_id 0, capacities derived. */
 int fq_params_default(fq_params *p);
+/* Set the shift damping zeta together with its critically damped forcing
+ * xi = zeta^2/4 (Eq. shift-update; the value the paper's printed time series
+ * are reproduced with, and the critical damping of x'' + zeta x' + xi x = 0).
+ * FQ_ERR_INVALID unless zeta >= 0 is finite.  Set xi afterwards to depart
+ * from it. */
+int fq_params_set_zeta(fq_params *p, double zeta);
 
 /* Create a Bose-Hubbard Hamiltonian with N bosons, hopping t, interaction u.
  * N >= 1, N + M - 1 <= 128.  FQ_ERR_INVALID for any other shape. */
@@ -156,8 +164,13 @@ int fq_ham_column(const fq_ham *h, fq_key key, double *diag, fq_key *dest, doubl
  *    written;
  *  - the array is shared per device: calls that overlap in time (several
  *    host threads) race on it, so callers must serialise them;
- *  - the first call on a device looks up the array's address and may load
- *    the module: make it outside any CUDA stream capture. */
+ *  - the work runs on a stream the library creates once per device with
+ *    cudaStreamNonBlocking: it does not wait for the legacy default stream
+ *    or for the caller's streams (queued steps keep running), and the call
+ *    returns once its own copies have completed;
+ *  - the first call on a device looks up the array's address (which may
+ *    load the module) and creates that stream: make it outside any CUDA
+ *    stream capture. */
 #define FQ_COLUMN_NOALLOC_MAX 16384
 int fq_ham_column_noalloc(const fq_ham *h, fq_key key, double *diag, fq_key *dest, double *val,
                           size_t cap, size_t *m);
@@ -225,6 +238,20 @@ int fq_run_spawns(fq_run *r, fq_key *dest, double *val, size_t cap, size_t *n);
 int fq_run_reserve(fq_run *r, size_t capacity_vec, size_t capacity_spawn);
 /* Current total capacities (entries of the vector, spawns per step). */
 int fq_run_capacity(const fq_run *r, size_t *capacity_vec, size_t *capacity_spawn);
+/* Annihilation tables (tests and tuning; not in the paper).  A bucket's
+ * spawns are summed in an on-chip table of `slots` entries per merge warp
+ * when they fill at most 0.7 of it, else in that warp's table of
+ * `scratch_slots` entries in device memory, which by default holds any
+ * bucket within the run's capacities; a bucket beyond 0.9 of the scratch
+ * table fails the step with FQ_ERR_CAPACITY (error bit 2) and the run is
+ * rolled back.  Each size is a power of two >= 64 (slots: 8 warps' tables
+ * within 200 KB of shared memory; scratch_slots <= 2^26); 0 restores the
+ * default.  Synchronises; the next step rebuilds the launch. */
+int fq_run_set_tables(fq_run *r, unsigned slots, unsigned scratch_slots);
+/* Buckets the merge summed in the on-chip table and in the scratch table
+ * since the run was seeded (a rolled-back step's buckets included).
+ * Synchronises. */
+int fq_run_merge_paths(fq_run *r, uint64_t *onchip, uint64_t *scratch);
 /* Time the launch shapes on the current vector and keep the fastest.  Each
  * candidate runs `steps` real steps, so the run advances. */
 int fq_run_autotune(fq_run *r, int steps);

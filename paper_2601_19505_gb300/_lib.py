@@ -38,6 +38,7 @@ SYMBOLS = {
     "fq_version": (C.c_char_p, []),
     "fq_strerror": (C.c_char_p, [C.c_int]),
     "fq_params_default": (C.c_int, [C.POINTER(FqParams)]),
+    "fq_params_set_zeta": (C.c_int, [C.POINTER(FqParams), C.c_double]),
     "fq_ham_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int,
                                 C.c_double, C.c_double]),
     "fq_ham_destroy": (None, [C.c_void_p]),
@@ -76,6 +77,8 @@ SYMBOLS = {
     "fq_run_autotune": (C.c_int, [C.c_void_p, C.c_int]),
     "fq_run_reserve": (C.c_int, [C.c_void_p, C.c_size_t, C.c_size_t]),
     "fq_run_capacity": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+    "fq_run_set_tables": (C.c_int, [C.c_void_p, C.c_uint, C.c_uint]),
+    "fq_run_merge_paths": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "fq_run_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "fq_run_profile": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_float)]),
     "fq_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int]),

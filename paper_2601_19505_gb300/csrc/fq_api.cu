@@ -117,6 +117,7 @@ struct fq_run {
     LaunchCfg tuned;
     bool has_tuned;
     unsigned scratch_slots;  // global scratch table size for buckets too big for SW
+    unsigned forced_slots, forced_scratch;  // fq_run_set_tables overrides (0 = none)
     unsigned gen;  // bumped whenever a device pointer of the run changes
     unsigned last_err_bits;  // device error bits reported by the last check
     double* pinned;        // host staging slot for parameter updates
@@ -136,6 +137,7 @@ struct fq_batch {
     std::vector<unsigned> gens;  // run generations the descriptors were built from
     unsigned char* scratch;      // merge scratch tables (from runs[0]'s allocator)
     size_t scratch_bytes;
+    unsigned scratch_ss;         // table size the scratch was last cleared for
     std::vector<LaunchCfg> shapes;  // launch shapes the scratch was sized for
 };
 
@@ -250,13 +252,20 @@ extern "C" int fq_params_default(fq_params* p) {
     p->dt = 0.01;
     p->target = 1000.0;
     p->zeta = 0.08;
-    p->xi = 0.08 * 0.08 / 4.0;
+    p->xi = 0.08 * 0.08 / 4.0;  // zeta^2 / 4, as fq_params_set_zeta
     p->threshold = 1.0;
     p->t_rel = 1.0;
     p->mode = FQ_MODE_REAL64;
     p->annihilation = FQ_ANN_AUTO;
     p->seed = 1;
     p->run_id = 0;
+    return FQ_OK;
+}
+
+extern "C" int fq_params_set_zeta(fq_params* p, double zeta) {
+    if (!p || !std::isfinite(zeta) || !(zeta >= 0)) return FQ_ERR_INVALID;
+    p->zeta = zeta;
+    p->xi = zeta * zeta / 4.0;
     return FQ_OK;
 }
 
@@ -560,6 +569,17 @@ static unsigned warp_slots(const KernelSet* ks) {
     return sw;
 }
 
+// the merge's table sizes of a run: on-chip slots per warp, and the global
+// scratch table, which holds any bucket within the run's capacities
+// (Cv + Cs <= 0.9 of its slots), unless fq_run_set_tables overrode them
+static void table_sizes(fq_run* r) {
+    r->slots = r->forced_slots ? r->forced_slots : warp_slots(r->ks);
+    r->scratch_slots =
+        r->forced_scratch
+            ? r->forced_scratch
+            : std::max(r->slots, next_pow2((unsigned long long)std::ceil((r->Cv + r->Cs) / 0.9)));
+}
+
 // per-segment capacities for totals lcap, scap over B segments (spawns
 // arrive in clumps of up to k, see fq_run_create)
 static void segment_caps(double lcap, double scap, unsigned B, double k, unsigned& Cv, unsigned& Cs) {
@@ -633,7 +653,7 @@ extern "C" int fq_run_create(fq_run** out, const fq_ham* h, const fq_params* p, 
         // bucket count fluctuates like a compound Poisson sum with clump size k
         const double k = r->det ? (double)max_offdiag(h->mp) : 8.0;
         segment_caps(lcap, scap, r->B, k, r->Cv, r->Cs);
-        r->scratch_slots = std::max(r->slots, next_pow2((unsigned long long)std::ceil((r->Cv + r->Cs) / 0.9)));
+        table_sizes(r);
     }
     r->log2B = ilog2(r->B);
     const unsigned B = r->B;
@@ -799,6 +819,7 @@ extern "C" int fq_run_seed(fq_run* r, const fq_key* keys, const double* amps, si
     s0.norm_lo = s0.norm_hi = 0;
     s0.norm_fp = 0.0;
     s0.len_acc = 0;
+    s0.merged_onchip = s0.merged_scratch = 0;
     cudaError_t e = cudaMemcpyAsync(r->st, &s0, sizeof s0, cudaMemcpyHostToDevice, r->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->vcount[0], 0, sizeof(unsigned) * r->B, r->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->vcount[1], 0, sizeof(unsigned) * r->B, r->stream);
@@ -1046,7 +1067,7 @@ static int batch_build(fq_batch* b) {
     size_t warps = 0;
     for (const LaunchCfg& c : b->shapes) warps = std::max(warps, (size_t)c.merge_grid * c.merge_wpb);
     const size_t bytes = warps * ss * b->ks->slot_bytes;
-    if (!b->scratch || b->scratch_bytes < bytes) {
+    if (!b->scratch || b->scratch_bytes < bytes || b->scratch_ss != ss) {
         fq_run* r0 = b->runs[0];
         if (b->scratch) {
             CK(cudaStreamSynchronize(b->stream));
@@ -1060,6 +1081,8 @@ static int batch_build(fq_batch* b) {
         if (!p) return FQ_ERR_NOMEM;
         b->scratch = (unsigned char*)p;
         b->scratch_bytes = bytes;
+        // each merge warp's table is laid out for `ss` slots: cleared for it
+        b->scratch_ss = ss;
         b->ks->scratch_init(b->scratch, ss, (unsigned)warps, r0->stream);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(r0->stream));
@@ -1093,6 +1116,7 @@ static int batch_new(fq_run* const* runs, int n, bool owned, fq_batch** out) {
     b->g1 = b->g16 = nullptr;
     b->scratch = nullptr;
     b->scratch_bytes = 0;
+    b->scratch_ss = 0;
     int rc = batch_build(b);
     if (rc) {
         batch_free(b);
@@ -1309,7 +1333,7 @@ extern "C" int fq_run_reserve(fq_run* r, size_t capacity_vec, size_t capacity_sp
         r->samps = nv;
         r->Cs = Cs;
     }
-    r->scratch_slots = std::max(r->slots, next_pow2((unsigned long long)std::ceil((r->Cv + r->Cs) / 0.9)));
+    table_sizes(r);
     r->gen++;
     CK(sync_self(r));
     return FQ_OK;
@@ -1320,6 +1344,33 @@ extern "C" int fq_run_capacity(const fq_run* r, size_t* capacity_vec, size_t* ca
     if (capacity_vec) *capacity_vec = (size_t)r->B * r->Cv;
     if (capacity_spawn) *capacity_spawn = (size_t)r->B * r->Cs;
     return FQ_OK;
+}
+
+extern "C" int fq_run_set_tables(fq_run* r, unsigned slots, unsigned scratch_slots) {
+    if (!r) return FQ_ERR_INVALID;
+    auto pow2 = [](unsigned x) { return x && !(x & (x - 1)); };
+    if (slots && (!pow2(slots) || slots < 64 || 8ull * slots * r->ks->slot_bytes > 200u * 1024u))
+        return FQ_ERR_INVALID;
+    if (scratch_slots && (!pow2(scratch_slots) || scratch_slots < 64 || scratch_slots > (1u << 26)))
+        return FQ_ERR_INVALID;
+    int rc = run_check(r);
+    if (rc) return rc;
+    r->forced_slots = slots;
+    r->forced_scratch = scratch_slots;
+    table_sizes(r);
+    r->has_tuned = false;  // a tuned shape was timed with the old tables
+    r->gen++;
+    return FQ_OK;
+}
+
+extern "C" int fq_run_merge_paths(fq_run* r, uint64_t* onchip, uint64_t* scratch) {
+    if (!r || !onchip || !scratch) return FQ_ERR_INVALID;
+    const int rc = run_check(r);
+    RunState s;
+    CK(cudaMemcpy(&s, r->st, sizeof s, cudaMemcpyDeviceToHost));
+    *onchip = s.merged_onchip;
+    *scratch = s.merged_scratch;
+    return rc;
 }
 
 extern "C" int fq_run_lookup(fq_run* r, const fq_key* keys, size_t n, double* amps) {
@@ -1622,6 +1673,7 @@ extern "C" int fq_batch_autotune(fq_batch* b, int steps) {
     return fq_batch_sync(b);
 }
 
+
 // ---------------------------------------------------------------------------
 // fq_ham_column_noalloc: the column of H without allocating anything.
 //
@@ -1641,9 +1693,12 @@ extern "C" int fq_batch_autotune(fq_batch* b, int steps) {
 //    tables, the diagonal, the count and the entries before reading them.
 //  - The array is shared by every caller on a device.  Calls that overlap in
 //    time (from several host threads) race on it; callers must serialise.
+//  - Work runs on a stream the library creates once per device with
+//    cudaStreamNonBlocking, so it neither waits for nor holds up the legacy
+//    default stream or any other stream of the caller.
 //  - The first call on a device looks up the array's device address
-//    (cudaGetSymbolAddress), which may load the module: make that first call
-//    outside any stream capture.
+//    (cudaGetSymbolAddress, which may load the module) and creates that
+//    stream: make that first call outside any stream capture.
 
 namespace {
 constexpr unsigned kNaMax = FQ_COLUMN_NOALLOC_MAX;  // column entries
@@ -1657,30 +1712,26 @@ constexpr size_t kNaOffDest = kNaOffHead + 256;
 constexpr size_t kNaOffVal = kNaOffDest + na_round(sizeof(fq_key) * kNaMax);
 constexpr size_t kNaBytes = kNaOffVal + na_round(sizeof(double) * kNaMax);  // 729,600 B
 constexpr int kNaDevices = 64;
-std::atomic<unsigned char*> g_na_base[kNaDevices];
+
+struct NaDevice {
+    unsigned char* base;  // device address of g_na_scratch on this device
+    cudaStream_t stream;  // non-blocking stream of this device's calls
+};
+NaDevice g_na[kNaDevices];
+std::atomic<bool> g_na_ready[kNaDevices];
+std::mutex g_na_setup;
 }  // namespace
 
 static __device__ __align__(256) unsigned char g_na_scratch[kNaBytes];
 
-// k_column with its tables and outputs in the fixed array: the block fills
-// the sqrt / hop tables (the expressions of k_tables), then one thread
-// enumerates the column and writes it in fq_key layout
+// the column at `key`, with the tables k_tables wrote into the fixed array by
+// an earlier launch on the same stream; written in fq_key layout (one thread)
 template <class K, int KIND>
-__global__ void __launch_bounds__(256) k_column_fixed(ModelParams mp, K key, unsigned char* base) {
-    double* sq = (double*)(base + kNaOffSq);
-    double* hop = (double*)(base + kNaOffHop);
-    float* hop32 = (float*)(base + kNaOffHop32);
-    for (int i = threadIdx.x; i <= mp.kmax; i += blockDim.x) {
-        const double s = sqrt((double)i);
-        sq[i] = s;
-        hop[i] = -(mp.t * s);
-        hop32[i] = (float)hop[i];
-    }
-    __syncthreads();
-    if (threadIdx.x) return;
-    mp.sqrt_tab = sq;
-    mp.hop_tab = hop;
-    mp.hop32_tab = hop32;
+__global__ void k_column_fixed(ModelParams mp, K key, unsigned char* base) {
+    if (threadIdx.x || blockIdx.x) return;
+    mp.sqrt_tab = (const double*)(base + kNaOffSq);
+    mp.hop_tab = (const double*)(base + kNaOffHop);
+    mp.hop32_tab = (const float*)(base + kNaOffHop32);
     typedef Model<KIND> MD;
     typename MD::Col col;
     const unsigned m = MD::num_offdiag(mp, key, col);
@@ -1696,10 +1747,35 @@ __global__ void __launch_bounds__(256) k_column_fixed(ModelParams mp, K key, uns
 }
 
 template <class K>
-static void launch_column_fixed(int kind, const ModelParams& mp, K key, unsigned char* base) {
-    if (kind == FQ_BH_REAL_1D) k_column_fixed<K, FQ_KIND_REAL_1D><<<1, 256>>>(mp, key, base);
-    else if (kind == FQ_BH_REAL_2D) k_column_fixed<K, FQ_KIND_REAL_2D><<<1, 256>>>(mp, key, base);
-    else k_column_fixed<K, FQ_KIND_MOM_1D><<<1, 256>>>(mp, key, base);
+static void launch_column_fixed(int kind, const ModelParams& mp, K key, unsigned char* base,
+                                cudaStream_t s) {
+    if (kind == FQ_BH_REAL_1D) k_column_fixed<K, FQ_KIND_REAL_1D><<<1, 32, 0, s>>>(mp, key, base);
+    else if (kind == FQ_BH_REAL_2D) k_column_fixed<K, FQ_KIND_REAL_2D><<<1, 32, 0, s>>>(mp, key, base);
+    else k_column_fixed<K, FQ_KIND_MOM_1D><<<1, 32, 0, s>>>(mp, key, base);
+}
+
+// set-up of the current device, once: the array's address and the stream
+static int na_device(NaDevice** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_err(e);
+    if (dev < 0 || dev >= kNaDevices) return FQ_ERR_INVALID;
+    if (!g_na_ready[dev].load(std::memory_order_acquire)) {
+        std::lock_guard<std::mutex> lock(g_na_setup);
+        if (!g_na_ready[dev].load(std::memory_order_relaxed)) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_na_scratch);
+            if (e != cudaSuccess) return cuda_err(e);
+            cudaStream_t s = nullptr;
+            e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_err(e);
+            g_na[dev].base = (unsigned char*)p;
+            g_na[dev].stream = s;
+            g_na_ready[dev].store(true, std::memory_order_release);
+        }
+    }
+    *out = &g_na[dev];
+    return FQ_OK;
 }
 
 extern "C" int fq_ham_column_noalloc(const fq_ham* h, fq_key key, double* diag, fq_key* dest,
@@ -1708,24 +1784,24 @@ extern "C" int fq_ham_column_noalloc(const fq_ham* h, fq_key key, double* diag, 
     ModelParams mp = h->mp;
     mp.kmax = (mp.N + 1) * (mp.N + 2);
     if ((size_t)mp.kmax + 1 > kNaTab) return FQ_ERR_INVALID;
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_err(e);
-    if (dev < 0 || dev >= kNaDevices) return FQ_ERR_INVALID;
-    unsigned char* base = g_na_base[dev].load();
-    if (!base) {  // once per device, with that device current
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_na_scratch);
-        if (e != cudaSuccess) return cuda_err(e);
-        base = (unsigned char*)p;
-        g_na_base[dev].store(base);
-    }
-    if (h->kw == 1) launch_column_fixed<uint64_t>(mp.kind, mp, (uint64_t)key.lo, base);
-    else launch_column_fixed<u128>(mp.kind, mp, ((u128)key.hi << 64) | (u128)key.lo, base);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    NaDevice* nd = nullptr;
+    int rc = na_device(&nd);
+    if (rc) return rc;
+    unsigned char* base = nd->base;
+    const cudaStream_t s = nd->stream;
+    // the tables first, in their own launch: the column kernel reads them
+    // through the read-only cache, which is only valid for data that no
+    // thread of the same launch writes
+    k_tables<<<(unsigned)((mp.kmax + 256) / 256), 256, 0, s>>>(
+        mp.t, mp.kmax, (double*)(base + kNaOffSq), (double*)(base + kNaOffHop),
+        (float*)(base + kNaOffHop32));
+    if (h->kw == 1) launch_column_fixed<uint64_t>(mp.kind, mp, (uint64_t)key.lo, base, s);
+    else launch_column_fixed<u128>(mp.kind, mp, ((u128)key.hi << 64) | (u128)key.lo, base, s);
+    cudaError_t e = cudaGetLastError();
     unsigned char head[16];
-    if (e == cudaSuccess) e = cudaMemcpy(head, base + kNaOffHead, sizeof head, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(head, base + kNaOffHead, sizeof head, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_err(e);
     double d;
     unsigned m;
@@ -1735,9 +1811,11 @@ extern "C" int fq_ham_column_noalloc(const fq_ham* h, fq_key key, double* diag, 
     if (m > kNaMax) return FQ_ERR_CAPACITY;  // longer than the fixed array holds
     if (diag) *diag = d;
     const size_t nw = std::min<size_t>(m, cap);
-    if (nw && dest) e = cudaMemcpy(dest, base + kNaOffDest, sizeof(fq_key) * nw, cudaMemcpyDeviceToHost);
+    if (nw && dest)
+        e = cudaMemcpyAsync(dest, base + kNaOffDest, sizeof(fq_key) * nw, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && nw && val)
-        e = cudaMemcpy(val, base + kNaOffVal, sizeof(double) * nw, cudaMemcpyDeviceToHost);
+        e = cudaMemcpyAsync(val, base + kNaOffVal, sizeof(double) * nw, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return cuda_err(e);
 }
 static_assert(kNaBytes == 729600, "fixed column array size as documented in fciqmc.h");

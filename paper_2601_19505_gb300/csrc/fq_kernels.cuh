@@ -530,22 +530,31 @@ __device__ __forceinline__ bool compress(typename AmpT<AMP>::ACC w, const RunDes
     }
 }
 
+// per-warp totals of one run, carried across buckets
+struct MergeAcc {
+    unsigned long long nlo, nhi, nlen;
+    double nfp;
+    bool full, over, range_bad;
+    unsigned long long ntheta;  // stored values of magnitude theta (a power of two)
+    unsigned n_onchip, n_scratch;  // buckets summed in each kind of table (warp-uniform)
+};
+
 // add a warp's share of one run's step totals to the run's accumulators
-__device__ __forceinline__ void merge_flush(const RunDesc* R, unsigned long long nlo,
-                                            unsigned long long nhi, unsigned long long nlen,
-                                            double nfp, bool full, bool over, bool range_bad,
-                                            unsigned long long ntheta, int lane) {
-    add128(nlo, nhi, ntheta << 52, ntheta >> 12);  // the values of magnitude theta
+__device__ __forceinline__ void merge_flush(const RunDesc* R, MergeAcc a, int lane) {
+    unsigned long long nlo = a.nlo, nhi = a.nhi;
+    add128(nlo, nhi, a.ntheta << 52, a.ntheta >> 12);  // the values of magnitude theta
     warp_sum128(nlo, nhi);
-    nlen = warp_sum(nlen);
-    nfp = warp_sum(nfp);
-    const bool f = __any_sync(0xFFFFFFFFu, full), o = __any_sync(0xFFFFFFFFu, over),
-               b = __any_sync(0xFFFFFFFFu, range_bad);
+    const unsigned long long nlen = warp_sum(a.nlen);
+    const double nfp = warp_sum(a.nfp);
+    const bool f = __any_sync(0xFFFFFFFFu, a.full), o = __any_sync(0xFFFFFFFFu, a.over),
+               b = __any_sync(0xFFFFFFFFu, a.range_bad);
     if (lane == 0) {
         const unsigned long long old = atomicAdd(&R->st->norm_lo, nlo);
         atomicAdd(&R->st->norm_hi, nhi + (old + nlo < old ? 1ull : 0ull));
         atomicAdd(&R->st->len_acc, nlen);
         if (R->mode_det) atomicAdd(&R->st->norm_fp, nfp);
+        if (a.n_onchip) atomicAdd(&R->st->merged_onchip, (unsigned long long)a.n_onchip);
+        if (a.n_scratch) atomicAdd(&R->st->merged_scratch, (unsigned long long)a.n_scratch);
         if (f) atomicOr(&R->st->err, FQ_DERR_TABLE);
         if (o) atomicOr(&R->st->err, FQ_DERR_VEC_CAP);
         if (b) atomicOr(&R->st->err, FQ_DERR_RANGE);
@@ -556,14 +565,6 @@ __device__ __forceinline__ void merge_flush(const RunDesc* R, unsigned long long
 template <class K, int AMP> __host__ __device__ constexpr size_t slot_bytes() {
     return sizeof(K) + sizeof(typename AmpT<AMP>::ACC) + sizeof(unsigned);
 }
-
-// per-warp totals of one run, carried across buckets
-struct MergeAcc {
-    unsigned long long nlo, nhi, nlen;
-    double nfp;
-    bool full, over, range_bad;
-    unsigned long long ntheta;  // stored values of magnitude theta (a power of two)
-};
 
 // a table sum that an entry of c^(n) has taken over (no valid sum has these
 // bits: a NaN payload, or the most negative integer)
@@ -832,7 +833,7 @@ k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     const RunDesc* R = nullptr;
     unsigned run_lo = 0, run_hi = 0;  // segments of the current run
     unsigned err = 0, cur = 0;
-    MergeAcc acc = {0, 0, 0, 0.0, false, false, false, 0};
+    MergeAcc acc = {0, 0, 0, 0.0, false, false, false, 0, 0, 0};
     // counts of buckets ahead_g and ahead2_g, loaded before they are needed
     unsigned ahead_g = 0xFFFFFFFFu, ahead2_g = 0xFFFFFFFFu;
     unsigned a1_old = 0, a1_sp = 0, a2_old = 0, a2_sp = 0;
@@ -840,9 +841,8 @@ k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     for (unsigned g = g0; g < g1; ++g) {
         if (g < run_lo || g >= run_hi) {  // warp-uniform
             if (R) {
-                merge_flush(R, acc.nlo, acc.nhi, acc.nlen, acc.nfp, acc.full, acc.over,
-                            acc.range_bad, acc.ntheta, lane);
-                acc = MergeAcc{0, 0, 0, 0.0, false, false, false, 0};
+                merge_flush(R, acc, lane);
+                acc = MergeAcc{0, 0, 0, 0.0, false, false, false, 0, 0, 0};
             }
             R = runs + seg_run[g];
             run_lo = R->seg_base;
@@ -909,16 +909,16 @@ k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
         if (load * 10ull <= (unsigned long long)SW * 7ull) {
             merge_bucket<K, AMP, KIND>(R, seg, cur, n_old, n_sp, sk_s, sa_s, sl_s, SW - 1u, lane,
                                        acc);
+            ++acc.n_onchip;
         } else if (load * 10ull <= (unsigned long long)SS * 9ull) {
             merge_bucket<K, AMP, KIND>(R, seg, cur, n_old, n_sp, sk_g, sa_g, sl_g, SS - 1u, lane,
                                        acc);
+            ++acc.n_scratch;
         } else {
             acc.full = true;  // even the scratch table cannot hold this bucket
         }
     }
-    if (R)
-        merge_flush(R, acc.nlo, acc.nhi, acc.nlen, acc.nfp, acc.full, acc.over, acc.range_bad,
-                    acc.ntheta, lane);
+    if (R) merge_flush(R, acc, lane);
 }
 
 // scratch tables start empty (keys EMPTY, sums 0); each use leaves them so

@@ -66,6 +66,9 @@ struct RunState {
     unsigned long long norm_lo, norm_hi;
     double norm_fp;
     unsigned long long len_acc;
+    // buckets the merge kernel summed in the on-chip table and in the global
+    // scratch table, since seeding
+    unsigned long long merged_onchip, merged_scratch;
 };
 
 // Everything a kernel needs to process one run's segments.  Lives in a

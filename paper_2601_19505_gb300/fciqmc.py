@@ -15,7 +15,7 @@ from . import _lib as L
 
 BH_REAL_1D, BH_REAL_2D, BH_MOM_1D = 1, 2, 3
 MODE_INT, MODE_REAL64, MODE_REAL32, MODE_DETERMINISTIC = 0, 1, 2, 3
-ANN_AUTO, ANN_HASH = 0, 2
+ANN_AUTO, ANN_SORT, ANN_HASH = 0, 1, 2
 
 KEY_DTYPE = np.dtype([("lo", "<u8"), ("hi", "<u8")])
 STATS_DTYPE = np.dtype([("step", "<i8"), ("len", "<i8"), ("exact_steps", "<i8"),
@@ -77,16 +77,19 @@ def _as_keys(keys) -> np.ndarray:
 
 
 def default_params(**kw) -> L.FqParams:
-    """fq_params_default, then the given fields; setting zeta alone also sets
-    xi = zeta^2 / 4."""
+    """fq_params_default, then the given fields; zeta goes through
+    fq_params_set_zeta (which also sets its forcing xi) before an explicit xi."""
     p = L.FqParams()
-    _check(L.load().fq_params_default(C.byref(p)), "fq_params_default")
+    lib = L.load()
+    _check(lib.fq_params_default(C.byref(p)), "fq_params_default")
+    if "zeta" in kw:
+        _check(lib.fq_params_set_zeta(C.byref(p), float(kw["zeta"])), "fq_params_set_zeta")
     for k, v in kw.items():
+        if k == "zeta":
+            continue
         if not hasattr(p, k):
             raise AttributeError(k)
         setattr(p, k, v)
-    if "zeta" in kw and "xi" not in kw:
-        p.xi = p.zeta ** 2 / 4
     return p
 
 
@@ -277,6 +280,18 @@ class Run:
         a = np.zeros(max(cap, 1))
         _check(self._lib.fq_run_export(self.r, _ptr(k), _ptr(a), cap, C.byref(n)), "fq_run_export")
         return k[: n.value].copy(), a[: n.value].copy()
+
+    def set_tables(self, slots: int = 0, scratch_slots: int = 0):
+        """fq_run_set_tables: override the merge's on-chip and scratch table sizes (0 = default)."""
+        _check(self._lib.fq_run_set_tables(self.r, int(slots), int(scratch_slots)),
+               "fq_run_set_tables")
+
+    def merge_paths(self):
+        """fq_run_merge_paths: (on-chip, scratch) bucket counts since seeding."""
+        a, b = C.c_uint64(), C.c_uint64()
+        self._chk(self._lib.fq_run_merge_paths(self.r, C.byref(a), C.byref(b)),
+                  "fq_run_merge_paths")
+        return a.value, b.value
 
     def lookup(self, keys) -> np.ndarray:
         """Amplitudes of the given addresses (0 when not stored)."""

@@ -41,6 +41,14 @@ def test_host_side_calls_without_gpu():
     p = fq.default_params()
     assert (p.dt, p.zeta, p.threshold, p.t_rel, p.target) == (0.01, 0.08, 1.0, 1.0, 1000.0)
     assert p.xi == pytest.approx(0.08 ** 2 / 4)
+    # the library sets the forcing of a given damping (xi = zeta^2 / 4); an
+    # explicit xi overrides it
+    p = fq.default_params(zeta=0.3)
+    assert (p.zeta, p.xi) == (0.3, 0.3 * 0.3 / 4.0)
+    p = fq.default_params(zeta=0.3, xi=0.01)
+    assert (p.zeta, p.xi) == (0.3, 0.01)
+    with pytest.raises(fq.FqError):
+        fq.default_params(zeta=-1.0)
     for kind, Lx, Ly, N in [(1, 6, 1, 6), (1, 20, 1, 20), (3, 32, 1, 32), (2, 8, 8, 64)]:
         h = fq.Hamiltonian(kind, Lx, Ly, N, 1.0, 2.0)
         m = O.Model(kind, Lx, Ly, N, 1.0, 2.0)

@@ -215,24 +215,86 @@ def test_launch_shape_and_profile():
     (O.MOM_1D, 6, 1, 6, 4.0, 1), (O.REAL_2D, 3, 3, 4, 3.0, 1)],
     ids=["real1d-f64", "real1d-f32", "mom1d-f64", "real2d-f64"])
 def test_energy_agrees_with_exact_diagonalisation(case):
-    """GPU runs with the default parameters (N_t = 1000): after 1000 steps of
-    equilibration, the blocked projected energy and shift of the next 3000
-    steps agree with exact diagonalisation.  On these small vectors the GPU
-    follows the oracle's trajectory for the same seed (whose estimates are
-    within 1 sigma here), but spawns are summed in arrival order, so an FP
-    run is not guaranteed to repeat bit for bit: the bound is 3 sigma (2
-    sigma is checked on the reproducible integer-walker run of c1 and on
-    the oracle's own runs)."""
+    """GPU runs with N_t = 1e4 and seeds 1..4: after 1000 steps of
+    equilibration, the blocked projected energy (ratio of means, Sec. 4.2)
+    and the blocked shift of the next 5000 steps, each pooled over the four
+    seeds by inverse-variance weights, lie within 2 sigma of exact
+    diagonalisation.  (At the default N_t = 1e3 the 6/6 projected energy
+    carries a population-control bias of about 2 pooled sigma, Sec. 3.3; ten
+    times the walkers shrink it by about sqrt(10) relative to the error.)"""
     import oracle.blocking as BL
     import oracle.ed as ED
     kind, Lx, Ly, N, u, mode = case
     h, m = pair(kind, Lx, Ly, N, 1.0, u)
-    g = fq().Run(h, fq().default_params(mode=mode, seed=1))
-    g.seed_default(10.0)
-    g.step(4000)
-    hist = g.history()
     e0 = ED.lowest(m, 1)[0]
-    r = BL.ratio_of_means(list(hist["hproj"][1000:]), list(hist["vproj"][1000:]))
-    s = BL.blocking_analysis(list(hist["shift"][1000:]))
-    assert abs(r["ratio"] - e0) < 3 * r["err"], (r, e0)
-    assert abs(s["mean"] - e0) < 3 * s["err"], (s, e0)
+    est = {"projected": [], "shift": []}
+    for seed in (1, 2, 3, 4):
+        g = fq().Run(h, fq().default_params(mode=mode, seed=seed, target=1e4))
+        g.seed_default(10.0)
+        g.step(6000)
+        hist = g.history()
+        g.close()
+        assert len(hist) == 6000
+        r = BL.ratio_of_means(list(hist["hproj"][1000:]), list(hist["vproj"][1000:]))
+        s = BL.blocking_analysis(list(hist["shift"][1000:]))
+        est["projected"].append((r["ratio"], r["err"]))
+        est["shift"].append((s["mean"], s["err"]))
+    for name, v in est.items():
+        w = np.array([1.0 / e ** 2 for _, e in v])
+        mean = float(np.dot([x for x, _ in v], w) / w.sum())
+        err = float(1.0 / np.sqrt(w.sum()))
+        assert abs(mean - e0) < 2 * err, (name, mean, err, e0, v)
+
+
+@pytest.mark.parametrize("mode", ["REAL64", "REAL32", "INT"])
+@pytest.mark.parametrize("model", [MODELS[1], MODELS[3]], ids=["real1d-64bit", "real2d-128bit"])
+def test_scratch_table_path_matches_oracle(model, mode):
+    """Buckets whose spawns fill more than 0.7 of a merge warp's on-chip table
+    are summed in that warp's table in device memory.  A small target (few
+    buckets) and a 20k-entry seeded vector put thousands of spawns in every
+    bucket, so every bucket takes that path (counted by the library); the
+    steps still match the oracle (FP64 to 1e-12, integers bit-exact)."""
+    h, m = pair(*model)
+    mcode = {"REAL64": 1, "REAL32": 2, "INT": 0}[mode]
+    keys, amps = seeded_vector(m, 20000, 31, mode=mode)
+    g, o = runs(h, m, mode=mcode, dt=0.001, target=1000.0, seed=6,
+                capacity_vec=200000, capacity_spawn=2000000)
+    g.seed(fq().keys_from_ints(keys), amps, -2.0, step=100)
+    o.seed(keys, amps, -2.0, step=100)
+    rtol = {"REAL64": 1e-12, "REAL32": 1e-5, "INT": 0.0}[mode]
+    for s in range(3):
+        g.step(1)
+        o.step(1)
+        assert_same_vector(g.export(), o.export(), rtol=rtol, what="step %d" % s)
+    onchip, scratch = g.merge_paths()
+    assert scratch > 0 and scratch >= 3 * onchip, (onchip, scratch)
+    gh, oh = g.history(), o.history()
+    for f in ("len", "exact_steps", "inexact_steps", "n_spawns"):
+        assert np.array_equal(gh[f], oh[f]), f
+
+
+def test_scratch_table_overflow_rolls_back():
+    """A bucket beyond 0.9 of the scratch table fails the step: FQ_ERR_CAPACITY
+    with error bit 2 (a full annihilation table), the run rolled back to its
+    last completed step; with the default tables it then steps like the
+    oracle."""
+    h, m = pair(*MODELS[1])
+    keys, amps = seeded_vector(m, 20000, 31)
+    g, o = runs(h, m, dt=0.001, target=1000.0, seed=6, capacity_vec=200000,
+                capacity_spawn=2000000)
+    g.seed(fq().keys_from_ints(keys), amps, -2.0, step=100)
+    o.seed(keys, amps, -2.0, step=100)
+    g.set_tables(64, 64)  # 57 spawns at most per bucket; these buckets hold thousands
+    g.step(1)
+    assert g.sync() == -3
+    assert g.error_bits() & 4
+    st = g.stats()
+    assert st["step"] == 100 and st["len"] == len(keys)
+    assert_same_vector(g.export(), o.export(), rtol=0.0, what="after the rollback")
+    with pytest.raises(fq().FqError):
+        g.set_tables(100, 0)  # not a power of two
+    g.set_tables(0, 0)
+    g.step(1)
+    o.step(1)
+    assert_same_vector(g.export(), o.export(), rtol=1e-12, what="after the failed step")
+    assert g.merge_paths()[1] > 0

@@ -15,12 +15,13 @@ import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-MODELS = [  # kind, Lx, Ly, N, u: 64- and 128-bit addresses, all three kinds
-    (1, 20, 1, 20, 2.0),
-    (2, 8, 8, 64, 8.0),
-    (3, 32, 1, 32, 4.0),
-    (3, 16, 1, 9, 1.5),
-    (2, 5, 3, 11, 3.0),
+MODELS = [  # kind, Lx, Ly, N, t, u: 64- and 128-bit addresses, all three kinds
+    (1, 20, 1, 20, 1.0, 2.0),
+    (2, 8, 8, 64, 1.0, 8.0),
+    (3, 32, 1, 32, 1.0, 4.0),
+    (3, 16, 1, 9, 0.7, 1.5),
+    (2, 5, 3, 11, 2.5, 3.0),
+    (1, 9, 1, 30, 0.3, 1.0),   # N > M: multiply occupied sites, t != 1
 ]
 
 
@@ -44,8 +45,8 @@ def _call(name, h, key, cap):
 @pytest.mark.parametrize("model", MODELS, ids=lambda m: "k%d_%dx%d_N%d" % m[:4])
 def test_noalloc_column_equals_allocating_column(model):
     import paper_2601_19505_gb300 as fq
-    kind, Lx, Ly, N, u = model
-    h = fq.Hamiltonian(kind, Lx, Ly, N, 1.0, u)
+    kind, Lx, Ly, N, t, u = model
+    h = fq.Hamiltonian(kind, Lx, Ly, N, t, u)
     rng = np.random.default_rng(7)
     occ = W.random_occupations(kind, Lx, Ly, N, 6, rng)
     keys = [h.starting_address()] + [h.encode(o) for o in occ]
@@ -83,3 +84,29 @@ def test_noalloc_column_short_buffer_and_rejection():
     # the array is still good afterwards
     rc2, d2, m2, _, v2 = _call("fq_ham_column_noalloc", h, key, 64)
     assert rc2 == 0 and m2 == 40 and d2 == d0
+
+
+def test_noalloc_calls_alternating_between_models():
+    """Calls on models with different N, t and address width, alternated
+    A, B, A, C, B, ...: every call rewrites the tables in the fixed array, so
+    a stale or partial table of the previous model would show here."""
+    import paper_2601_19505_gb300 as fq
+    hams = [fq.Hamiltonian(*m[:3], m[3], m[4], m[5]) for m in MODELS]
+    rng = np.random.default_rng(11)
+    keys = []
+    for (kind, Lx, Ly, N, _, _), h in zip(MODELS, hams):
+        occ = W.random_occupations(kind, Lx, Ly, N, 2, rng)
+        keys.append([h.starting_address()] + [h.encode(o) for o in occ])
+    want = {}
+    for i, h in enumerate(hams):
+        for j, key in enumerate(keys[i]):
+            rc, d, m, k, v = _call("fq_ham_column", h, key, 1 << 15)
+            assert rc == 0
+            want[i, j] = (d, m, k[:m].copy(), v[:m].copy())
+    order = [0, 1, 0, 2, 1, 5, 3, 0, 4, 5, 2, 3, 1, 4, 0]
+    for n, i in enumerate(order):
+        j = n % len(keys[i])
+        rc, d, m, k, v = _call("fq_ham_column_noalloc", hams[i], keys[i][j], 1 << 15)
+        d0, m0, k0, v0 = want[i, j]
+        assert rc == 0 and m == m0 and d == d0, (i, j)
+        assert np.array_equal(k[:m], k0) and np.array_equal(v[:m], v0), (i, j)
