@@ -71,6 +71,17 @@ enum { FQ_MODE_INT = 0, FQ_MODE_REAL64 = 1, FQ_MODE_REAL32 = 2, FQ_MODE_DETERMIN
  * FQ_ERR_INVALID).  AUTO picks HASH. */
 enum { FQ_ANN_AUTO = 0, FQ_ANN_SORT = 1, FQ_ANN_HASH = 2 };
 
+/* Where vector compression Pi acts (Sec. 7.1).  LATE (default, Eq.
+ * late-comp): on each address's summed value after annihilation.  EARLY (Eq.
+ * early-comp): on every spawn and every diagonal term on its own, before any
+ * sum; a spawn below the threshold that compression drops is never written,
+ * and the summed values are stored as they are (some may lie below the
+ * threshold).  Real-valued walkers only: INT and DETERMINISTIC runs ignore
+ * it.  The draw of a spawn's compression is the draw that picked it (attempt
+ * a of its source), that of entry k of an exact column the draw of stream k,
+ * and that of a diagonal term stream 0xFFFFFFFD of its address. */
+enum { FQ_COMPRESS_LATE = 0, FQ_COMPRESS_EARLY = 1 };
+
 enum {
     FQ_OK = 0,
     FQ_ERR_INVALID = -1,  /* bad argument or handle state                        */
@@ -87,13 +98,15 @@ enum {
  * vec-compression with 1 -> theta).  t_rel: semistochastic threshold; a column
  * is spawned exactly when |c_i| t_rel >= m_i (Sec. 7.1).  mode: FQ_MODE_*.
  * annihilation: FQ_ANN_*.  seed, run_id: key of the counter-based random
- * draws.  capacity_vec, capacity_spawn: maximum occupied entries of the
- * vector and spawn entries per step (0 = derived from target and threshold). */
+ * draws.  compression: FQ_COMPRESS_*.  capacity_vec, capacity_spawn: maximum
+ * occupied entries of the vector and spawn entries per step (0 = derived from
+ * target and threshold). */
 typedef struct {
     double dt, target, zeta, xi, threshold, t_rel;
     int32_t mode, annihilation;
     uint64_t seed;
-    uint32_t run_id, reserved;
+    uint32_t run_id;
+    int32_t compression;
     size_t capacity_vec, capacity_spawn;
 } fq_params;
 
@@ -273,6 +286,26 @@ void fq_batch_destroy(fq_batch *b);
 int fq_batch_step(fq_batch *b, int64_t n);
 int fq_batch_sync(fq_batch *b);
 int fq_batch_autotune(fq_batch *b, int steps);
+
+/* Replica overlaps (Sec. 4.3, Eq. RayleighQuotientReplica): with R = 2..8
+ * replicas in one batch (one Hamiltonian, equal sizes; statistically
+ * independent through their run_id), record after every step, for every pair
+ * A < B in the order (0,1), (0,2), ..., (1,2), ..., the vector-vector product
+ * c_A^T c_B and the vector-operator-vector products c_A^T G2(d_k) c_B of the
+ * density-density correlator G2(d) = (1/M) sum_i n_i (n_{i+d} - delta_{d0})
+ * (Eq. g2; 1D real space only, 0 <= d_k < M, n_g2 <= 16; n_g2 = 0 records the
+ * dot products alone).  The variational energy of Sec. 4.3 is then the ratio
+ * of the means of (S_A + S_B)/2 c_A^T c_B and c_A^T c_B (shifts from each
+ * run's history).  Each pair's sums over segments are added in a fixed
+ * order, so repeated runs give identical rows.  Replaces any earlier
+ * setting; FQ_ERR_INVALID for runs of different shapes or sizes. */
+int fq_batch_set_overlaps(fq_batch *b, const int *g2_d, int n_g2);
+/* Move out the overlap rows recorded since the last call, oldest first, at
+ * most cap of them (*n = rows written).  A row is `width` doubles: the step,
+ * then per pair c_A^T c_B followed by its n_g2 G2 products; width =
+ * 1 + P (1 + n_g2) with P = R (R - 1) / 2.  The ring keeps at least the last
+ * 1024 rows; steps that failed (rolled back) leave no row.  Synchronises. */
+int fq_batch_overlaps(fq_batch *b, double *rows, size_t cap, size_t *n, int *width);
 
 #ifdef __cplusplus
 }

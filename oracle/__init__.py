@@ -31,6 +31,7 @@ _OUT = os.path.join(_HERE, "_build", "libfqoracle.so")
 
 REAL_1D, REAL_2D, MOM_1D = 1, 2, 3
 MODE_INT, MODE_REAL64, MODE_REAL32, MODE_DETERMINISTIC = 0, 1, 2, 3
+COMPRESS_LATE, COMPRESS_EARLY = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -55,7 +56,7 @@ class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("target", C.c_double), ("zeta", C.c_double),
                 ("xi", C.c_double), ("threshold", C.c_double), ("t_rel", C.c_double),
                 ("mode", C.c_int32), ("pad0", C.c_int32), ("seed", C.c_uint64),
-                ("run_id", C.c_uint32), ("pad1", C.c_uint32)]
+                ("run_id", C.c_uint32), ("compression", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -113,6 +114,9 @@ def lib():
         L.or_exact_norm_of.argtypes = [C.c_void_p, C.c_long, C.c_double, C.c_int]
         L.or_shift_update.restype = C.c_double
         L.or_shift_update.argtypes = [C.c_double] * 7
+        L.or_overlap.argtypes = [vp, vp, C.c_void_p, C.c_int, dp]
+        L.or_g2_diag.restype = C.c_double
+        L.or_g2_diag.argtypes = [vp, kp, C.c_int]
         L.or_build_sparse.restype = C.c_long
         L.or_build_sparse.argtypes = [vp, kp, C.c_long, C.c_void_p, C.c_long, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]
@@ -220,6 +224,10 @@ class Model:
         lib().or_column(self.h, C.byref(kk), _ptr(keys), _ptr(vals), m)
         return [key_int(keys[i]) for i in range(m)], vals[:m].copy()
 
+    def g2_diag(self, key, d: int) -> float:
+        """G2(d) on one address (Eq. g2), 1D real space."""
+        return lib().or_g2_diag(self.h, C.byref(key_of(key)), int(d))
+
     def column_bruteforce(self, key, cap: int = 1 << 16):
         kk = key_of(key)
         keys = np.zeros(cap, dtype=KEY_DT)
@@ -251,7 +259,7 @@ def default_params(**kw) -> Params:
     """Defaults recovered from the paper's printed time series: dt = 0.01,
     zeta = 0.08, xi = zeta^2 / 4, threshold 1, t_rel 1, target 1000."""
     p = Params(dt=0.01, target=1000.0, zeta=0.08, xi=0.08 ** 2 / 4, threshold=1.0, t_rel=1.0,
-               mode=MODE_REAL64, pad0=0, seed=1, run_id=0, pad1=0)
+               mode=MODE_REAL64, pad0=0, seed=1, run_id=0, compression=COMPRESS_LATE)
     for k, v in kw.items():
         setattr(p, k, v)
     if "zeta" in kw and "xi" not in kw:
@@ -325,6 +333,15 @@ class Run:
         pre, post = C.c_double(), C.c_double()
         lib().or_point(self.h, C.byref(key_of(key)), C.byref(pre), C.byref(post))
         return pre.value, post.value
+
+
+def overlap(a: Run, b: Run, g2_d=()) -> np.ndarray:
+    """[c_A^T c_B, c_A^T G2(d) c_B for d in g2_d] of two runs of one model (Sec. 4.3)."""
+    d = np.ascontiguousarray(g2_d, dtype=np.int32)
+    out = np.zeros(1 + len(d))
+    if lib().or_overlap(a.h, b.h, _ptr(d), len(d), out.ctypes.data_as(C.POINTER(C.c_double))):
+        raise ValueError("G2 needs 1D real space and 0 <= d < M")
+    return out
 
 
 def start_run(model: Model, params: Params, weight: float = 10.0, shift=None) -> Run:

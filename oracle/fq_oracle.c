@@ -25,6 +25,9 @@
  *   - Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) as the random source;
  *     the paper does not name its generator, so the keyed layout of the draws
  *     is this project's own definition.
+ *   - Early compression (Sec. 7.1, Eq. early-comp) as the alternative to the
+ *     late compression above, and the replica overlaps c_A^T c_B and
+ *     c_A^T G2(d) c_B of Sec. 4.3 (Eqs. RayleighQuotientReplica, g2).
  * Readings of places where the paper is silent or garbled are stated at each
  * function.  Compile with -ffp-contract=off: no fused multiply-adds.
  */
@@ -51,7 +54,8 @@ typedef struct {
     double dt, target, zeta, xi, threshold, t_rel;
     int32_t mode, pad0;
     uint64_t seed;
-    uint32_t run_id, pad1;
+    uint32_t run_id;
+    int32_t compression; /* 0: late (Eq. late-comp), 1: early (Eq. early-comp) */
 } or_params;
 
 typedef struct {
@@ -465,9 +469,34 @@ static double store_round(int mode, double v) {
     return mode == OR_REAL32 ? (double)(float)v : v;
 }
 
+static int compress_one(const or_params *pr, const uint32_t w[4], double v, double *out);
+
+/* Early compression applies to real-valued walkers only (integer walkers
+ * are integral already; the deterministic limit compresses nothing). */
+static int early(const or_params *pr) {
+    return pr->compression == 1 && (pr->mode == OR_REAL64 || pr->mode == OR_REAL32);
+}
+
+/* Push one spawn or diagonal term; under early compression (Sec. 7.1) it is
+ * first compressed on its own with the 53-bit uniform of draw `w`, and a
+ * dropped value is not pushed.  Returns 1 when a value was pushed. */
+static int push_term(clist *out, const or_params *pr, const uint32_t w[4], okey dest, okey src,
+                     uint32_t a, int is_spawn, double v) {
+    if (early(pr)) {
+        double o;
+        if (!compress_one(pr, w, v, &o)) return 0;
+        v = o;
+    }
+    push(out, dest, src, a, is_spawn, v);
+    return 1;
+}
+
 /* Every contribution of source entry (key, c) at step `step`, shift `shift`:
  * the diagonal term and the spawns (Eq. column-compression).  Counts
- * exact/inexact columns. */
+ * exact/inexact columns.  Under early compression the draws of the
+ * individual compressions are: the pick's own draw (attempt a) for a
+ * stochastic spawn, the draw of stream k for entry k of an exact column, and
+ * stream 0xFFFFFFFD for the diagonal term, all keyed by the source. */
 static void source_contribs(const or_model *md, const or_params *pr, uint32_t step, double shift,
                             okey key, double c, clist *out, int64_t *n_exact, int64_t *n_inexact,
                             int64_t *n_spawns) {
@@ -528,8 +557,9 @@ static void source_contribs(const or_model *md, const or_params *pr, uint32_t st
             const float coef = (-dtf) * cf;
             for (long k = 0; k < m; ++k) {
                 const float v = (float)col[k].val * coef;
-                push(out, col[k].key, key, (uint32_t)k, 1, (double)v);
-                (*n_spawns)++;
+                uint32_t w[4] = {0, 0, 0, 0};
+                if (early(pr)) draw(pr, step, (uint32_t)k, h, w);
+                *n_spawns += push_term(out, pr, w, col[k].key, key, (uint32_t)k, 1, (double)v);
             }
         } else {
             (*n_inexact)++;
@@ -540,12 +570,13 @@ static void source_contribs(const or_model *md, const or_params *pr, uint32_t st
                 draw(pr, step, a, h, w);
                 uint32_t k = pick(w, (uint32_t)m);
                 const float v = (float)col[k].val * coef;
-                push(out, col[k].key, key, a, 1, (double)v);
-                (*n_spawns)++;
+                *n_spawns += push_term(out, pr, w, col[k].key, key, a, 1, (double)v);
             }
         }
         const float d = cf + cf * delta;
-        push(out, key, key, 0, 0, (double)d);
+        uint32_t wd[4] = {0, 0, 0, 0};
+        if (early(pr)) draw(pr, step, 0xFFFFFFFDu, h, wd);
+        push_term(out, pr, wd, key, key, 0, 0, (double)d);
         free(col);
         return;
     }
@@ -559,8 +590,10 @@ static void source_contribs(const or_model *md, const or_params *pr, uint32_t st
         double coef = (-dt) * c;
         for (long k = 0; k < m; ++k) {
             double v = col[k].val * coef;
-            push(out, col[k].key, key, (uint32_t)k, 1, store_round(pr->mode, v));
-            (*n_spawns)++;
+            uint32_t w[4] = {0, 0, 0, 0};
+            if (early(pr)) draw(pr, step, (uint32_t)k, h, w);
+            *n_spawns += push_term(out, pr, w, col[k].key, key, (uint32_t)k, 1,
+                                   store_round(pr->mode, v));
         }
     } else {
         (*n_inexact)++;
@@ -572,11 +605,12 @@ static void source_contribs(const or_model *md, const or_params *pr, uint32_t st
             draw(pr, step, a, h, w);
             uint32_t k = pick(w, (uint32_t)m);
             double v = col[k].val * coef;
-            push(out, col[k].key, key, a, 1, store_round(pr->mode, v));
-            (*n_spawns)++;
+            *n_spawns += push_term(out, pr, w, col[k].key, key, a, 1, store_round(pr->mode, v));
         }
     }
-    push(out, key, key, 0, 0, c * factor);
+    uint32_t wd[4] = {0, 0, 0, 0};
+    if (early(pr)) draw(pr, step, 0xFFFFFFFDu, h, wd);
+    push_term(out, pr, wd, key, key, 0, 0, c * factor);
     free(col);
 }
 
@@ -593,6 +627,24 @@ static int compress(const or_model *md, const or_params *pr, uint32_t step, okey
     draw(pr, step, 0xFFFFFFFFu, rng_h(md, key), r);
     if (uniform53(r) < aw / pr->threshold) {
         *out = store_round(pr->mode, copysign(pr->threshold, w));
+        return 1;
+    }
+    return 0;
+}
+
+/* Early compression (Sec. 7.1, Eq. early-comp): Pi applied to the
+ * contribution of one column before any sum.  Reading: the text says each
+ * spawn is compressed individually, so every spawn value and the diagonal
+ * term d_i are compressed on their own; nothing is compressed after the
+ * sum.  The value v is kept when |v| >= theta, else it becomes sign(v) theta
+ * with probability |v| / theta (as in late compression), decided by the
+ * 53-bit uniform of the draw `w`.  Returns 0 when the value is dropped. */
+static int compress_one(const or_params *pr, const uint32_t w[4], double v, double *out) {
+    if (v == 0.0) return 0;
+    double av = fabs(v);
+    if (av >= pr->threshold) { *out = v; return 1; }
+    if (uniform53(w) < av / pr->threshold) {
+        *out = store_round(pr->mode, copysign(pr->threshold, v));
         return 1;
     }
     return 0;
@@ -791,7 +843,8 @@ static int one_step(or_run *r) {
         }
         if (r->pr.mode == OR_REAL32) w = (double)wf;
         double out;
-        if (compress(&r->md, &r->pr, step, cl.c[i].dest, w, &out)) {
+        if (early(&r->pr) ? (out = w) != 0.0
+                                   : compress(&r->md, &r->pr, step, cl.c[i].dest, w, &out)) {
             nv[nn].key = cl.c[i].dest;
             nv[nn].amp = out;
             nn++;
@@ -895,9 +948,62 @@ int or_point(const void *p, const okey *jkey, double *pre, double *post) {
     free(cl.c);
     *pre = w;
     double out = 0.0;
-    if (!compress(&r->md, &r->pr, step, *jkey, w, &out)) out = 0.0;
+    if (early(&r->pr)) out = w;
+    else if (!compress(&r->md, &r->pr, step, *jkey, w, &out)) out = 0.0;
     *post = out;
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* replica overlaps (Sec. 4.3)                                              */
+
+/* Eq. g2: G2(d) = (1/M) sum_i n_i (n_{i+d} - delta_{d,0}) is diagonal in the
+ * real-space occupation basis; sites i + d are taken around the periodic
+ * ring of M sites (1D real space). */
+static double g2_diag(const or_model *md, const uint8_t *occ, int d) {
+    long long s = 0;
+    for (int i = 0; i < md->M; ++i)
+        s += (long long)occ[i] * ((long long)occ[(i + d) % md->M] - (d == 0 ? 1 : 0));
+    return (double)s / (double)md->M;
+}
+
+/* For two stored vectors of one model: out[0] = c_A^T c_B and
+ * out[1 + k] = c_A^T G2(d_k) c_B (k < nd; 1D real space only), the
+ * vector-vector and vector-operator-vector products of Sec. 4.3 that
+ * Eq. RayleighQuotientReplica averages.  Both vectors are sorted by
+ * address, so the common addresses are found by walking the two lists
+ * together; the terms c_A,j c_B,j and G2(d)_jj c_A,j c_B,j are added in
+ * ascending address order.  Returns -1 for G2 requested outside 1D real
+ * space or d outside [0, M). */
+int or_overlap(const void *pa, const void *pb, const int *d, int nd, double *out) {
+    const or_run *a = (const or_run *)pa, *b = (const or_run *)pb;
+    if (nd > 0 && a->md.kind != OR_REAL_1D) return -1;
+    for (int k = 0; k < nd; ++k)
+        if (d[k] < 0 || d[k] >= a->md.M) return -1;
+    for (int k = 0; k <= nd; ++k) out[k] = 0.0;
+    long i = 0, j = 0;
+    while (i < a->n && j < b->n) {
+        int c = key_cmp(a->vec[i].key, b->vec[j].key);
+        if (c < 0) { ++i; continue; }
+        if (c > 0) { ++j; continue; }
+        double p = a->vec[i].amp * b->vec[j].amp;
+        out[0] += p;
+        if (nd > 0) {
+            uint8_t occ[OR_MAXM];
+            decode_key(&a->md, a->vec[i].key, occ);
+            for (int k = 0; k < nd; ++k) out[1 + k] += g2_diag(&a->md, occ, d[k]) * p;
+        }
+        ++i; ++j;
+    }
+    return 0;
+}
+
+/* G2(d)_jj of one address (for pins against the definition). */
+double or_g2_diag(const void *pm, const okey *k, int d) {
+    const or_model *md = (const or_model *)pm;
+    uint8_t occ[OR_MAXM];
+    decode_key(md, *k, occ);
+    return g2_diag(md, occ, d);
 }
 
 /* ------------------------------------------------------------------------ */

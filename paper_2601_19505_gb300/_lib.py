@@ -15,7 +15,7 @@ class FqParams(C.Structure):
     _fields_ = [("dt", C.c_double), ("target", C.c_double), ("zeta", C.c_double),
                 ("xi", C.c_double), ("threshold", C.c_double), ("t_rel", C.c_double),
                 ("mode", C.c_int32), ("annihilation", C.c_int32), ("seed", C.c_uint64),
-                ("run_id", C.c_uint32), ("reserved", C.c_uint32),
+                ("run_id", C.c_uint32), ("compression", C.c_int32),
                 ("capacity_vec", C.c_size_t), ("capacity_spawn", C.c_size_t)]
 
 
@@ -81,6 +81,9 @@ SYMBOLS = {
     "fq_run_merge_paths": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "fq_run_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "fq_run_profile": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_float)]),
+    "fq_batch_set_overlaps": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "fq_batch_overlaps": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t),
+                                    C.POINTER(C.c_int)]),
     "fq_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int]),
     "fq_batch_destroy": (None, [C.c_void_p]),
     "fq_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),

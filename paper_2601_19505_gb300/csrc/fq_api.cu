@@ -139,6 +139,18 @@ struct fq_batch {
     size_t scratch_bytes;
     unsigned scratch_ss;         // table size the scratch was last cleared for
     std::vector<LaunchCfg> shapes;  // launch shapes the scratch was sized for
+    // replica overlaps (fq_batch_set_overlaps)
+    bool ov_on;
+    int ov_nq;
+    int ov_d[FQ_MAX_G2];
+    OverlapDesc* d_ov;
+    double* ov_part;
+    size_t ov_part_n;
+    double* ov_ring;
+    unsigned long long* ov_head;
+    unsigned ov_cap, ov_table;
+    int ov_grid, ov_wpb;
+    unsigned long long ov_read;  // rows handed out so far
 };
 
 // ---------------------------------------------------------------------------
@@ -487,6 +499,7 @@ static void fill_desc(const fq_run* r, RunDesc& d, unsigned seg_base) {
     d.theta32 = (float)r->prm.threshold;
     d.t_rel = r->prm.t_rel;
     d.trel_one = r->prm.t_rel == 1.0;
+    d.early = r->prm.compression == FQ_COMPRESS_EARLY && !r->det && r->amp != FQ_AMP_INT;
     {
         int e = 0;
         const double fr = r->det || r->amp == FQ_AMP_INT ? 0.0 : std::frexp(r->prm.threshold, &e);
@@ -601,6 +614,8 @@ extern "C" int fq_run_create(fq_run** out, const fq_ham* h, const fq_params* p, 
     if (p->mode != FQ_MODE_DETERMINISTIC && p->mode != FQ_MODE_INT && !(p->threshold > 0))
         return FQ_ERR_INVALID;
     if (p->annihilation != FQ_ANN_AUTO && p->annihilation != FQ_ANN_HASH) return FQ_ERR_INVALID;
+    if (p->compression != FQ_COMPRESS_LATE && p->compression != FQ_COMPRESS_EARLY)
+        return FQ_ERR_INVALID;
     if (p->mode == FQ_MODE_INT && p->target > 1e12) return FQ_ERR_INVALID;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return FQ_ERR_CUDA;
@@ -980,12 +995,17 @@ extern "C" int fq_run_set_target(fq_run* r, double t) {
 // ---------------------------------------------------------------------------
 // batches: descriptor table, graphs, stepping
 
+static void launch_overlaps(fq_batch* b, cudaStream_t s) {
+    if (b->ov_on) b->ks->overlap(b->d_desc, b->d_ov, b->ov_grid, b->ov_wpb, b->ov_table, s);
+}
+
 static void enqueue_steps(fq_batch* b, int n, cudaStream_t s) {
     const int nr = (int)b->runs.size();
     for (int i = 0; i < n; ++i) {
         b->ks->spawn(b->cfg, b->d_desc, b->d_seg_run, b->G, s);
         b->ks->merge(b->cfg, b->d_desc, b->d_seg_run, b->G, s);
         launch_shift(b->d_desc, nr, s);
+        launch_overlaps(b, s);
     }
 }
 
@@ -999,9 +1019,72 @@ static void batch_release(fq_batch* b) {
     b->d_seg_run = nullptr;
 }
 
+static void overlaps_free(fq_batch* b) {
+    if (b->d_ov) cudaFree(b->d_ov);
+    if (b->ov_part) cudaFree(b->ov_part);
+    if (b->ov_ring) cudaFree(b->ov_ring);
+    if (b->ov_head) cudaFree(b->ov_head);
+    b->d_ov = nullptr;
+    b->ov_part = b->ov_ring = nullptr;
+    b->ov_head = nullptr;
+    b->ov_part_n = 0;
+    b->ov_on = false;
+}
+
+// the overlap launch for the batch's current sizes: one table per warp with
+// at least twice the slots of the largest segment capacity
+static int overlaps_build(fq_batch* b) {
+    if (!b->ov_on) return FQ_OK;
+    unsigned cv = 0;
+    for (fq_run* r : b->runs) cv = std::max(cv, r->Cv);
+    const unsigned T = std::max(64u, next_pow2(2ull * cv));
+    const size_t slot = b->ks->overlap_slot_bytes;
+    int wpb = 4;
+    while (wpb > 1 && (size_t)wpb * T * slot > 200u * 1024u) wpb >>= 1;
+    if ((size_t)T * slot > 200u * 1024u) return FQ_ERR_INVALID;  // segments too large
+    const size_t smem = (size_t)wpb * T * slot;
+    CK(b->ks->prepare_overlap(smem));
+    const int R = (int)b->runs.size(), P = R * (R - 1) / 2;
+    const unsigned long long items = (unsigned long long)P * b->runs[0]->B;
+    b->ov_wpb = wpb;
+    b->ov_grid = (int)std::max<unsigned long long>(
+        1, std::min<unsigned long long>((unsigned long long)num_sms() * (8 / wpb),
+                                        (items + wpb - 1) / wpb));
+    b->ov_table = T;
+    const size_t need = (size_t)b->ov_grid * wpb * P * (1 + b->ov_nq);
+    if (need > b->ov_part_n) {
+        if (b->ov_part) cudaFree(b->ov_part);
+        b->ov_part = nullptr;
+        b->ov_part_n = 0;
+        CK(cudaMalloc((void**)&b->ov_part, sizeof(double) * need));
+        b->ov_part_n = need;
+    }
+    OverlapDesc od;
+    memset(&od, 0, sizeof od);
+    od.R = R;
+    od.P = P;
+    od.nq = b->ov_nq;
+    for (int k = 0; k < b->ov_nq; ++k) od.d[k] = b->ov_d[k];
+    int p = 0;
+    for (int a = 0; a < R; ++a)
+        for (int c = a + 1; c < R; ++c, ++p) {
+            od.pa[p] = a;
+            od.pb[p] = c;
+        }
+    od.B = b->runs[0]->B;
+    od.table = T;
+    od.part = b->ov_part;
+    od.ring = b->ov_ring;
+    od.head = b->ov_head;
+    od.cap = b->ov_cap;
+    CK(cudaMemcpy(b->d_ov, &od, sizeof od, cudaMemcpyHostToDevice));
+    return FQ_OK;
+}
+
 static void batch_free(fq_batch* b) {
     if (!b) return;
     batch_release(b);
+    overlaps_free(b);
     if (b->scratch) {
         fq_run* r0 = b->runs[0];
         if (r0->has_alloc) r0->alloc.free(r0->alloc.ctx, b->scratch, b->scratch_bytes, (void*)r0->stream);
@@ -1090,6 +1173,10 @@ static int batch_build(fq_batch* b) {
     for (LaunchCfg& c : b->shapes) {
         c.scratch = b->scratch;
         c.scratch_slots = ss;
+    }
+    {
+        const int rc = overlaps_build(b);
+        if (rc) return rc;
     }
     b->cfg = b->shapes[0];
     if (nr == 1 && b->runs[0]->has_tuned) {
@@ -1535,6 +1622,7 @@ static int autotune(fq_batch* b, int steps) {
         b->ks->merge(c, b->d_desc, b->d_seg_run, b->G, b->stream);
         e = cudaEventRecord(ev[3 * t + 2], b->stream);
         launch_shift(b->d_desc, nr, b->stream);
+        launch_overlaps(b, b->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     std::vector<double> ts(sc.size(), 0.0), tm(mc.size(), 0.0);
@@ -1664,6 +1752,63 @@ extern "C" int fq_batch_sync(fq_batch* b) {
         if (e && !rc) rc = e;
     }
     return rc;
+}
+
+extern "C" int fq_batch_set_overlaps(fq_batch* b, const int* g2_d, int n_g2) {
+    if (!b || n_g2 < 0 || n_g2 > FQ_MAX_G2 || (n_g2 && !g2_d)) return FQ_ERR_INVALID;
+    const int R = (int)b->runs.size();
+    if (R < 2 || R > FQ_MAX_REPLICAS) return FQ_ERR_INVALID;
+    const fq_run* r0 = b->runs[0];
+    for (const fq_run* r : b->runs)
+        if (r->B != r0->B || r->ham.mp.kind != r0->ham.mp.kind || r->ham.mp.M != r0->ham.mp.M ||
+            r->ham.mp.N != r0->ham.mp.N || r->ham.mp.Lx != r0->ham.mp.Lx)
+            return FQ_ERR_INVALID;
+    if (n_g2 && r0->ham.mp.kind != FQ_BH_REAL_1D) return FQ_ERR_INVALID;
+    for (int k = 0; k < n_g2; ++k)
+        if (g2_d[k] < 0 || g2_d[k] >= r0->ham.mp.M) return FQ_ERR_INVALID;
+    CK(cudaStreamSynchronize(b->stream));
+    overlaps_free(b);
+    const int P = R * (R - 1) / 2;
+    const size_t width = 1 + (size_t)P * (1 + n_g2);
+    b->ov_cap = (unsigned)std::min<size_t>(65536, std::max<size_t>(1024, (8u << 20) / width));
+    CK(cudaMalloc((void**)&b->d_ov, sizeof(OverlapDesc)));
+    CK(cudaMalloc((void**)&b->ov_ring, sizeof(double) * width * b->ov_cap));
+    CK(cudaMalloc((void**)&b->ov_head, sizeof(unsigned long long)));
+    CK(cudaMemset(b->ov_head, 0, sizeof(unsigned long long)));
+    b->ov_read = 0;
+    b->ov_nq = n_g2;
+    for (int k = 0; k < n_g2; ++k) b->ov_d[k] = g2_d[k];
+    b->ov_on = true;
+    // rebuild the descriptors and graphs with the overlap launch in each step
+    batch_release(b);
+    int rc = batch_build(b);
+    if (rc) overlaps_free(b);
+    return rc;
+}
+
+extern "C" int fq_batch_overlaps(fq_batch* b, double* rows, size_t cap, size_t* n, int* width) {
+    if (!b || !n || (cap && !rows)) return FQ_ERR_INVALID;
+    *n = 0;
+    if (!b->ov_on) return FQ_ERR_INVALID;
+    const int R = (int)b->runs.size(), P = R * (R - 1) / 2;
+    const size_t w = 1 + (size_t)P * (1 + b->ov_nq);
+    if (width) *width = (int)w;
+    CK(cudaStreamSynchronize(b->stream));
+    unsigned long long head = 0;
+    CK(cudaMemcpy(&head, b->ov_head, sizeof head, cudaMemcpyDeviceToHost));
+    unsigned long long first = b->ov_read;
+    if (head > b->ov_cap && first < head - b->ov_cap) first = head - b->ov_cap;
+    const size_t cnt = (size_t)std::min<unsigned long long>(head - first, cap);
+    for (size_t i = 0; i < cnt;) {
+        const unsigned pos = (unsigned)((first + i) % b->ov_cap);
+        const size_t chunk = std::min<size_t>(cnt - i, b->ov_cap - pos);
+        CK(cudaMemcpy(rows + i * w, b->ov_ring + (size_t)pos * w, sizeof(double) * w * chunk,
+                      cudaMemcpyDeviceToHost));
+        i += chunk;
+    }
+    b->ov_read = first + cnt;
+    *n = cnt;
+    return FQ_OK;
 }
 
 extern "C" int fq_batch_autotune(fq_batch* b, int steps) {

@@ -132,7 +132,10 @@ template <class K> __device__ __forceinline__ K run_starts(K k) { return k & ~(k
 //   key     = (seed_lo32, seed_hi32 ^ run_id * 0x9E3779B9)
 //   counter = (step, stream, h_lo32, h_hi32), h = KeyOps<K>::rng_h(address)
 //   stream  = attempt index for picks, 0xFFFFFFFF for vector compression,
-//             0xFFFFFFFE for integer diagonal rounding
+//             0xFFFFFFFE for integer diagonal rounding, 0xFFFFFFFD for the
+//             early compression of a diagonal term (a spawn's early
+//             compression reuses the draw of its pick, or of stream k for
+//             entry k of an exact column)
 
 __device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
 #pragma unroll
@@ -510,7 +513,12 @@ __device__ __forceinline__ void fixed_of(double x, int q, unsigned long long& lo
     const int E = (int)(b >> 52);
     const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
     const int sh = E - 1075 - q;  // |x| = m 2^(E - 1075)
-    if (E == 0 || sh < 0 || sh > 63) { bad = true; return; }
+    if (E == 0 || sh > 63) { bad = true; return; }
+    if (sh < 0) {  // below 2^(q + 52): exact only if the bits under 2^q are 0
+        if (sh < -52 || (m & ((1ull << -sh) - 1ull))) { bad = true; return; }
+        lo = m >> -sh;
+        return;
+    }
     lo = m << sh;
     hi = sh ? (m >> (64 - sh)) : 0ull;
 }
@@ -522,7 +530,12 @@ __device__ __forceinline__ void fixed_of(float x, int q, unsigned long long& lo,
     const int E = (int)(b >> 23);
     const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
     const int sh = E - 150 - q;  // |x| = m 2^(E - 150)
-    if (E == 0 || sh < 0 || sh > 63 + 40) { bad = true; return; }
+    if (E == 0 || sh > 63 + 40) { bad = true; return; }
+    if (sh < 0) {  // exact only if the bits under 2^q are 0
+        if (sh < -23 || (m & ((1ull << -sh) - 1ull))) { bad = true; return; }
+        lo = m >> -sh;
+        return;
+    }
     if (sh < 64) {
         lo = m << sh;
         hi = sh ? (m >> (64 - sh)) : 0ull;

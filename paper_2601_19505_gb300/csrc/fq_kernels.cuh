@@ -174,6 +174,7 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     int log2B = 0;
     double dt = 0.0;
     uint2 rkey = make_uint2(0, 0);
+    int early = 0;
     unsigned n_ex = 0, n_inex = 0, n_sp = 0;
 
     // the spawn whose bucket slot is being reserved (stored one spawn later)
@@ -232,6 +233,7 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
         dt = R->st->dt;
         stepno = (unsigned)(R->st->step + 1);
         rkey = make_uint2(R->key_x, R->key_y);
+        early = R->early;
     };
     // the next non-empty segment of the current run at or after g; the end
     // of the run's part of the range if none (n = its entry count)
@@ -279,6 +281,12 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
             CO hv;
             dest = MD::offdiag(mp, key, col, kk, hv);
             val = hv * cf;
+            if (early && !at_least_theta(val, R)) {
+                // early compression: the pick's own draw decides; entry kk of
+                // an exact column takes the draw of stream kk
+                if (ex) w = draw(rkey, stepno, a, KeyOps<K>::rng_h(key));
+                if (!pi_below(val, w, R)) return false;
+            }
         }
         return true;
     };
@@ -539,6 +547,32 @@ struct MergeAcc {
     unsigned n_onchip, n_scratch;  // buckets summed in each kind of table (warp-uniform)
 };
 
+// the two halves of Pi for one value, for early compression (Sec. 7.1, Eq.
+// early-comp), where the draw is the one of the spawn or a stream of its own:
+// |v| >= theta (kept as it is), decided on the bits
+template <class V>
+__device__ __forceinline__ bool at_least_theta(V v, const RunDesc* R) {
+    const unsigned long long ab = abs_dbits(v);
+    return R->theta_pow2 ? ab >= dbits(R->theta) : bdouble(ab) >= R->theta;
+}
+// |v| < theta: v becomes sign(v) theta with probability |v| / theta (the
+// 53-bit uniform of r against |v| / theta), else it is dropped (false)
+template <class V>
+__device__ __forceinline__ bool pi_below(V& v, uint4 r, const RunDesc* R) {
+    const unsigned long long ab = abs_dbits(v);
+    if (ab == 0) return false;
+    if (R->theta_pow2) {
+        if (!below_scaled(u53_of(r), ab, R->theta_exp)) return false;
+    } else {
+        if (!(uniform53(r) < bdouble(ab) / R->theta)) return false;
+    }
+    if constexpr (sizeof(V) == 8)
+        v = bdouble(dbits(R->theta) | (dbits(v) & 0x8000000000000000ull));
+    else
+        v = __uint_as_float(__float_as_uint(R->theta32) | (__float_as_uint(v) & 0x80000000u));
+    return true;
+}
+
 // add a warp's share of one run's step totals to the run's accumulators
 __device__ __forceinline__ void merge_flush(const RunDesc* R, MergeAcc a, int lane) {
     unsigned long long nlo = a.nlo, nhi = a.nhi;
@@ -590,12 +624,14 @@ template <class K, int AMP>
 __device__ __forceinline__ void merge_emit(const RunDesc* R, bool has, K key,
                                            typename AmpT<AMP>::ACC w, uint2 rkey, unsigned stepno,
                                            K* __restrict__ ok, typename AmpT<AMP>::A* __restrict__ oa,
-                                           unsigned Cv, int nq, int det, int lane, unsigned& nout,
-                                           MergeAcc& acc) {
+                                           unsigned Cv, int nq, int det, int early, int lane,
+                                           unsigned& nout, MergeAcc& acc) {
     typedef typename AmpT<AMP>::ACC ACC;
     typedef typename AmpT<AMP>::A A;
     ACC out = (ACC)0;
-    const bool keep = has && compress<AMP>(w, R, rkey, stepno, KeyOps<K>::rng_h(key), out);
+    // early compression stores the sums as they are (Eq. early-comp)
+    const bool keep = has && (early ? ((out = w) != (ACC)0)
+                                    : compress<AMP>(w, R, rkey, stepno, KeyOps<K>::rng_h(key), out));
     const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
     if (keep) {
         const unsigned pos = nout + (unsigned)__popc(bal & ((1u << lane) - 1u));
@@ -651,6 +687,7 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
     const uint2 rkey = make_uint2(R->key_x, R->key_y);
     const int nq = R->norm_q;
     const int det = R->mode_det;
+    const int early = R->early;
 
     // annihilation: every spawn to the bucket adds into its address; new
     // addresses join the list in warp order.  The next spawns are loaded
@@ -735,6 +772,14 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
                         w = (ACC)((long long)fl + (uniform53(r4) < x - fl ? 1 : 0));
                     }
                 }
+                if constexpr (AMP != FQ_AMP_INT) {
+                    // early compression: the diagonal term alone, with the
+                    // draw of stream 0xFFFFFFFD of its address
+                    if (early && !at_least_theta(w, R)) {
+                        const uint4 r4 = draw(rkey, stepno, 0xFFFFFFFDu, KeyOps<K>::rng_h(key));
+                        if (!pi_below(w, r4, R)) w = (ACC)0;
+                    }
+                }
                 if (n_sp) {
                     const int q = table_find(tk, mask, key);
                     if (q >= 0) {
@@ -743,7 +788,8 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
                     }
                 }
             }
-            merge_emit<K, AMP>(R, has, key, w, rkey, stepno, ok, oa, Cv, nq, det, lane, nout, acc);
+            merge_emit<K, AMP>(R, has, key, w, rkey, stepno, ok, oa, Cv, nq, det, early, lane, nout,
+                              acc);
         }
     }
     __syncwarp();
@@ -759,7 +805,8 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
             has = !is_taken(w);
             key = tk[q];
         }
-        merge_emit<K, AMP>(R, has, key, w, rkey, stepno, ok, oa, Cv, nq, det, lane, nout, acc);
+        merge_emit<K, AMP>(R, has, key, w, rkey, stepno, ok, oa, Cv, nq, det, early, lane, nout,
+                              acc);
     }
     __syncwarp();
     // projected-energy terms whose address falls in this bucket: read the
@@ -1028,6 +1075,151 @@ __global__ void __launch_bounds__(BLOCK) k_shift(const RunDesc* __restrict__ run
     }
     __syncthreads();
     if (s_ok && R->smax >= 0 && R->fac64) write_factors(R, s_S, st->dt);
+}
+
+// ---------------------------------------------------------------------------
+// replica overlaps (Sec. 4.3, Eq. RayleighQuotientReplica): for every pair
+// (A, B) of a batch's runs and every segment, A's entries go into the warp's
+// on-chip table and B's entries look up theirs; the products c_A,j c_B,j and
+// G2(d)_jj c_A,j c_B,j (Eq. g2) are summed per warp.  Each warp writes its
+// own partial sums (no atomics) and k_overlap_row adds them in warp order,
+// so the result does not depend on timing.
+
+// occupation numbers of the M modes of an address (modes without a run of
+// ones stay 0)
+template <class K>
+__device__ __forceinline__ void occupations(K key, int M, unsigned char* occ) {
+    for (int m = 0; m < M; ++m) occ[m] = 0;
+    K st = run_starts(key);
+    while (st) {
+        const int P = KeyOps<K>::ctz(st);
+        occ[P - KeyOps<K>::popc(key & KeyOps<K>::low(P))] = (unsigned char)run_from(key, P);
+        st &= st - 1;
+    }
+}
+
+template <class K, int AMP, int KIND>
+__global__ void __launch_bounds__(128) k_overlap(const RunDesc* __restrict__ runs,
+                                                 const OverlapDesc* __restrict__ od) {
+    typedef typename AmpT<AMP>::A A;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const unsigned T = od->table;
+    unsigned char* base = smem + (size_t)wib * T * (sizeof(K) + sizeof(double) + sizeof(unsigned));
+    K* const tk = (K*)base;
+    double* const ta = (double*)(base + (size_t)T * sizeof(K));
+    unsigned* const tl = (unsigned*)(base + (size_t)T * (sizeof(K) + sizeof(double)));
+    const K EMPTY = KeyOps<K>::empty();
+    for (unsigned q = lane; q < T; q += 32) tk[q] = EMPTY;
+    const unsigned gw = blockIdx.x * wpb + wib, nw = gridDim.x * wpb;
+    const int P = od->P, nq = od->nq, W = 1 + nq;
+    double* const part = od->part + (size_t)gw * P * W;
+    for (int i = lane; i < P * W; i += 32) part[i] = 0.0;
+    __syncwarp();
+    const unsigned B = od->B;
+    const unsigned long long total = (unsigned long long)P * B;
+    const unsigned long long i0 = total * gw / nw, i1 = total * (gw + 1) / nw;
+    double acc[1 + FQ_MAX_G2];
+    for (int q = 0; q < W; ++q) acc[q] = 0.0;
+    unsigned char occ[128];
+    int cur_p = -1;
+    const RunDesc *RA = nullptr, *RB = nullptr;
+    int ca = 0, cb = 0;
+    auto flush = [&]() {
+        for (int q = 0; q < W; ++q) {
+            const double v = warp_sum(acc[q]);
+            if (lane == 0) part[cur_p * W + q] = v;
+            acc[q] = 0.0;
+        }
+    };
+    for (unsigned long long it = i0; it < i1; ++it) {
+        const int p = (int)(it / B);
+        const unsigned seg = (unsigned)(it % B);
+        if (p != cur_p) {  // warp-uniform
+            if (cur_p >= 0) flush();
+            cur_p = p;
+            RA = runs + od->pa[p];
+            RB = runs + od->pb[p];
+            ca = RA->st->cur;
+            cb = RB->st->cur;
+        }
+        const unsigned na = min(RA->vcount[ca][seg], RA->Cv);
+        const unsigned nb = min(RB->vcount[cb][seg], RB->Cv);
+        if (!na || !nb) continue;
+        const K* ka = (const K*)RA->vkeys[ca] + (size_t)seg * RA->Cv;
+        const A* aa = (const A*)RA->vamps[ca] + (size_t)seg * RA->Cv;
+        const K* kb = (const K*)RB->vkeys[cb] + (size_t)seg * RB->Cv;
+        const A* ab = (const A*)RB->vamps[cb] + (size_t)seg * RB->Cv;
+        // A's entries (distinct addresses; the table has at least twice the
+        // slots, so an insert always finds one)
+        unsigned nl = 0;
+        for (unsigned j0 = 0; j0 < na; j0 += 32) {
+            const unsigned j = j0 + lane;
+            bool is_new = false;
+            int q = -1;
+            if (j < na) {
+                q = table_insert(tk, T - 1u, ka[j], is_new);
+                if (q >= 0) ta[q] = (double)aa[j];
+            }
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, is_new);
+            if (is_new) tl[nl + __popc(bal & ((1u << lane) - 1u))] = (unsigned)q;
+            nl += __popc(bal);
+        }
+        __syncwarp();
+        for (unsigned j0 = 0; j0 < nb; j0 += 32) {
+            const unsigned j = j0 + lane;
+            if (j < nb) {
+                const K key = kb[j];
+                const int q = table_find(tk, T - 1u, key);
+                if (q >= 0) {
+                    const double prod = ta[q] * (double)ab[j];
+                    acc[0] += prod;
+                    if (nq) {
+                        const int M = RA->mp.M;
+                        occupations(key, M, occ);
+                        for (int k = 0; k < nq; ++k) {
+                            const int d = od->d[k];
+                            long long sn = 0;
+                            for (int i = 0; i < M; ++i) {
+                                const int i2 = i + d < M ? i + d : i + d - M;
+                                sn += (long long)occ[i] * ((long long)occ[i2] - (d == 0 ? 1 : 0));
+                            }
+                            acc[1 + k] += ((double)sn / (double)M) * prod;
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        for (unsigned j = lane; j < nl; j += 32) tk[tl[j]] = EMPTY;
+        __syncwarp();
+    }
+    if (cur_p >= 0) flush();
+}
+
+// one row of overlaps: the per-warp partial sums added in warp order; no row
+// when a run of the batch failed this step (it will be rolled back)
+static __global__ void k_overlap_row(const RunDesc* __restrict__ runs,
+                                     const OverlapDesc* __restrict__ od, unsigned nwarps) {
+    __shared__ int ok;
+    const int n = od->P * (1 + od->nq);
+    if (threadIdx.x == 0) {
+        ok = 1;
+        for (int r = 0; r < od->R; ++r)
+            if (*(volatile unsigned*)&runs[r].st->err) ok = 0;
+    }
+    __syncthreads();
+    if (!ok) return;
+    const unsigned long long h = *od->head;
+    double* row = od->ring + (size_t)(h % od->cap) * (size_t)(1 + n);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        double s = 0.0;
+        for (unsigned w = 0; w < nwarps; ++w) s += od->part[(size_t)w * n + t];
+        row[1 + t] = s;
+    }
+    if (threadIdx.x == 0) row[0] = (double)runs[0].st->step;
+    __syncthreads();
+    if (threadIdx.x == 0) *od->head = h + 1;
 }
 
 // ---------------------------------------------------------------------------

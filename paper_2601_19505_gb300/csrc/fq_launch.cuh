@@ -118,6 +118,16 @@ template <class K, int AMP, int KIND> struct Launch {
         k_ref_terms<K, KIND><<<(n + 63) / 64, 64, 0, s>>>(mp, (const K*)refs, y, n, off,
                                                           (K*)tkeys, th, tv, tseg, log2B);
     }
+    static void overlap(const RunDesc* d, const OverlapDesc* od, int grid, int wpb,
+                        unsigned table, cudaStream_t s) {
+        const size_t smem = (size_t)wpb * table * (sizeof(K) + sizeof(double) + sizeof(unsigned));
+        k_overlap<K, AMP, KIND><<<grid, wpb * 32, smem, s>>>(d, od);
+        k_overlap_row<<<1, 256, 0, s>>>(d, od, (unsigned)(grid * wpb));
+    }
+    static cudaError_t prepare_overlap(size_t smem) {
+        return cudaFuncSetAttribute(k_overlap<K, AMP, KIND>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
     static KernelSet make() {
         KernelSet k;
         k.key_bytes = sizeof(K);
@@ -138,6 +148,9 @@ template <class K, int AMP, int KIND> struct Launch {
         k.column = column;
         k.ref_count = ref_count;
         k.ref_terms = ref_terms;
+        k.overlap = overlap;
+        k.prepare_overlap = prepare_overlap;
+        k.overlap_slot_bytes = sizeof(K) + sizeof(double) + sizeof(unsigned);
         return k;
     }
 };

@@ -32,6 +32,11 @@ struct KernelSet {
     void (*ref_terms)(const ModelParams&, const void* refs, const double* y, int n,
                       const unsigned* off, void* tkeys, double* th, double* tv, unsigned* tseg,
                       int log2B, cudaStream_t);
+    // replica overlaps: `grid` blocks of `wpb` warps, then the row
+    void (*overlap)(const RunDesc* runs, const OverlapDesc* od, int grid, int wpb,
+                    unsigned table, cudaStream_t);
+    size_t overlap_slot_bytes;  // one slot of an overlap table: key, FP64 amplitude, list entry
+    cudaError_t (*prepare_overlap)(size_t smem);
 };
 
 // kw = 64-bit words per address (1 or 2), amp = FQ_AMP_*, kind = FQ_KIND_*

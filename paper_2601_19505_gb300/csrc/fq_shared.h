@@ -81,6 +81,7 @@ struct RunDesc {
     float theta32;      // (float)theta
     int theta_pow2;     // theta = 2^theta_exp: compression decided in integers
     int theta_exp;
+    int early;          // early compression (Sec. 7.1): each spawn and diagonal term alone
     int norm_q;         // exact norm unit 2^norm_q
     int trel_one;       // t_rel == 1
     unsigned key_x, key_y;   // Philox key
@@ -108,6 +109,25 @@ struct RunDesc {
     unsigned n_ref_bkt;
     double* part_h;           // per-segment projected-energy partial sums
     double* part_v;
+};
+
+// Replica overlaps of a batch (Sec. 4.3): for every pair (A, B) of its runs,
+// c_A^T c_B and c_A^T G2(d_k) c_B (Eq. g2) after each step.  The runs share
+// one segment map (equal B), so segment b of A and of B hold the same
+// addresses' entries.
+#define FQ_MAX_REPLICAS 8
+#define FQ_MAX_G2 16
+struct OverlapDesc {
+    int R, P, nq;                  // runs, pairs, G2 distances
+    int d[FQ_MAX_G2];
+    int pa[FQ_MAX_REPLICAS * (FQ_MAX_REPLICAS - 1) / 2];
+    int pb[FQ_MAX_REPLICAS * (FQ_MAX_REPLICAS - 1) / 2];
+    unsigned B;                    // segments per run
+    unsigned table;                // slots of a warp's table (power of 2)
+    double* part;                  // per warp: P x (1 + nq) partial sums
+    double* ring;                  // rows of width 1 + P (1 + nq)
+    unsigned long long* head;      // rows written
+    unsigned cap;                  // rows the ring holds
 };
 
 struct LaunchCfg {

@@ -16,6 +16,7 @@ from . import _lib as L
 BH_REAL_1D, BH_REAL_2D, BH_MOM_1D = 1, 2, 3
 MODE_INT, MODE_REAL64, MODE_REAL32, MODE_DETERMINISTIC = 0, 1, 2, 3
 ANN_AUTO, ANN_SORT, ANN_HASH = 0, 1, 2
+COMPRESS_LATE, COMPRESS_EARLY = 0, 1
 
 KEY_DTYPE = np.dtype([("lo", "<u8"), ("hi", "<u8")])
 STATS_DTYPE = np.dtype([("step", "<i8"), ("len", "<i8"), ("exact_steps", "<i8"),
@@ -405,3 +406,19 @@ class Batch:
     def autotune(self, steps: int = 3):
         """Time the launch shapes on real steps and keep the fastest (the run advances)."""
         _check(self._lib.fq_batch_autotune(self.b, int(steps)), "fq_batch_autotune")
+
+    def set_overlaps(self, g2_d=()):
+        """fq_batch_set_overlaps: record c_A^T c_B and c_A^T G2(d) c_B after every step."""
+        d = np.ascontiguousarray(g2_d, dtype=np.int32)
+        _check(self._lib.fq_batch_set_overlaps(self.b, _ptr(d), len(d)), "fq_batch_set_overlaps")
+
+    def overlaps(self, cap: int = 1 << 16) -> np.ndarray:
+        """fq_batch_overlaps: the rows recorded since the last call, shape (rows, width)."""
+        w = C.c_int()
+        n = C.c_size_t()
+        _check(self._lib.fq_batch_overlaps(self.b, None, 0, C.byref(n), C.byref(w)),
+               "fq_batch_overlaps")
+        out = np.zeros((cap, w.value))
+        _check(self._lib.fq_batch_overlaps(self.b, _ptr(out), cap, C.byref(n), C.byref(w)),
+               "fq_batch_overlaps")
+        return out[: n.value].copy()

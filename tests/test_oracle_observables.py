@@ -1,0 +1,180 @@
+"""Pins of the oracle's replica overlaps and early compression (not GPU).
+
+Replica overlaps (Sec. 4.3): c_A^T c_B and c_A^T G2(d) c_B, with the
+density-density correlator G2(d) of Eq. g2.  Pinned by a combinatorial
+reading of G2 (ordered pairs of distinct bosons d sites apart), its sum rule
+over d, its d = 0 relation to the interaction energy, brute-force sums over
+exported vectors, and two-replica runs whose variational energy and <G2(d)>
+land within 2 sigma of exact diagonalisation.
+
+Early compression (Sec. 7.1, Eq. early-comp): every spawn and diagonal term is
+compressed on its own before annihilation.  Pinned by unbiasedness of one
+step, the absence of any sub-threshold term, and equality with late
+compression when the threshold compresses nothing.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.blocking as BL
+import oracle.ed as ED
+from conftest import golden
+
+
+def _pairs_at_distance(occ, d):
+    """Ordered pairs of distinct bosons whose sites differ by d around the ring."""
+    pos = [s for s, n in enumerate(occ) for _ in range(int(n))]
+    M = len(occ)
+    return sum(1 for a, b in itertools.permutations(range(len(pos)), 2)
+               if (pos[b] - pos[a]) % M == d)
+
+
+def test_g2_counts_boson_pairs_and_obeys_its_sum_rule():
+    m = O.Model(O.REAL_1D, 6, 1, 6, 1.0, 6.0)
+    basis = ED.basis_ints(ED.sparse_hamiltonian(m)[0])
+    assert len(basis) == 462
+    for k in basis:
+        occ = m.decode(k)
+        vals = [m.g2_diag(k, d) for d in range(6)]
+        for d in range(6):
+            assert vals[d] * 6 == pytest.approx(_pairs_at_distance(occ, d), abs=1e-12)
+        # sum over d of n_{i+d} is N: sum_d G2(d) = N (N - 1) / M
+        assert sum(vals) == pytest.approx(6 * 5 / 6, abs=1e-12)
+        # d = 0 counts on-site pairs: G2(0) = 2 H_jj / (u M) in real space
+        assert vals[0] == pytest.approx(2.0 * m.diagonal(k) / (6.0 * 6), abs=1e-12)
+
+
+def test_overlaps_equal_brute_force_sums():
+    m = O.Model(O.REAL_1D, 7, 1, 5, 1.0, 3.0)
+    ra = O.start_run(m, O.default_params(seed=3, run_id=0))
+    rb = O.start_run(m, O.default_params(seed=3, run_id=1))
+    ra.step(300)
+    rb.step(300)
+    ds = [0, 1, 2, 3]
+    got = O.overlap(ra, rb, ds)
+    (ka, aa), (kb, ab) = ra.export(), rb.export()
+    da = {O.key_int(k): a for k, a in zip(ka, aa)}
+    db = {O.key_int(k): a for k, a in zip(kb, ab)}
+    common = sorted(set(da) & set(db))
+    assert len(common) > 20
+    want = [sum(da[k] * db[k] for k in common)]
+    for d in ds:
+        want.append(sum(_pairs_at_distance(m.decode(k), d) / 7.0 * da[k] * db[k]
+                        for k in common))
+    assert np.allclose(got, want, rtol=1e-12)
+    # symmetric in the two replicas; a vector with itself gives sum c^2
+    assert np.allclose(O.overlap(rb, ra, ds), got, rtol=1e-13)
+    assert O.overlap(ra, ra)[0] == pytest.approx(float(np.dot(aa, aa)), rel=1e-13)
+    with pytest.raises(ValueError):
+        O.overlap(ra, rb, [7])
+
+
+def test_two_replicas_give_exact_variational_energy_and_g2():
+    """6/6, u = 6, two replicas (run ids 0 and 1) with N_t = 1e4: after 1000
+    steps, the variational energy (ratio of blocked means of
+    (S_A + S_B)/2 c_A^T c_B over c_A^T c_B, Sec. 4.3) and <G2(d)>
+    (Eq. RayleighQuotientReplica) lie within 2 sigma of the exact ground
+    state's values."""
+    m = O.Model(O.REAL_1D, 6, 1, 6, 1.0, 6.0)
+    e0, basis, v0 = ED.ground_state(m)
+    keys = ED.basis_ints(basis)
+    ds = [0, 1, 2, 3]
+    g2_exact = [float(np.dot(v0 * v0, [m.g2_diag(k, d) for k in keys]) / np.dot(v0, v0))
+                for d in ds]
+    ra = O.start_run(m, O.default_params(seed=1, run_id=0, target=1e4))
+    rb = O.start_run(m, O.default_params(seed=1, run_id=1, target=1e4))
+    rows = []
+    for _ in range(5000):
+        ra.step(1)
+        rb.step(1)
+        rows.append(O.overlap(ra, rb, ds).tolist() + [ra.state()[0], rb.state()[0]])
+    rows = np.array(rows)[1000:]
+    dot = rows[:, 0]
+    num = 0.5 * (rows[:, -2] + rows[:, -1]) * dot
+    ev = BL.ratio_of_means(list(num), list(dot))
+    assert abs(ev["ratio"] - e0) < 2 * ev["err"], (ev, e0)
+    for i, d in enumerate(ds):
+        r = BL.ratio_of_means(list(rows[:, 1 + i]), list(dot))
+        assert abs(r["ratio"] - g2_exact[i]) < 2 * r["err"], (d, r, g2_exact[i])
+    # the paper's printed variational estimate (N_t = 1e3), as context
+    g = golden("observables.json")
+    assert abs(g["variational_6x6"][0] - e0) < 2 * g["variational_6x6"][1]
+
+
+@pytest.mark.parametrize("mode", [O.MODE_REAL64, O.MODE_REAL32])
+def test_early_compression_step_is_unbiased(mode):
+    """E[c^(n+1)] = (1 + dt (S - H)) c^(n) also when every spawn and diagonal
+    term is compressed on its own (Eq. early-comp), over independently keyed
+    draws."""
+    m = O.Model(O.REAL_1D, 5, 1, 5, 1.0, 4.0)
+    basis, H = ED.dense_hamiltonian(m)
+    keys = ED.basis_ints(basis)
+    index = {k: i for i, k in enumerate(keys)}
+    rng = np.random.default_rng(7)
+    sel = rng.choice(len(keys), 25, replace=False)
+    amps = rng.exponential(2.0, size=25) * rng.choice([-1, 1], size=25)
+    amps[0] = 60.0   # an exact column
+    amps[1] = -0.3
+    c = np.zeros(len(keys))
+    c[sel] = amps
+    dt, S = 0.05, -1.0
+    want = (np.eye(len(keys)) + dt * (S * np.eye(len(keys)) - H)) @ c
+    run = O.Run(m, O.default_params(mode=mode, dt=dt, compression=O.COMPRESS_EARLY))
+    R = 3000
+    acc = np.zeros(len(keys))
+    acc2 = np.zeros(len(keys))
+    for r in range(R):
+        run.seed([keys[i] for i in sel], amps, S, step=1000 + r)
+        run.step(1)
+        k, a = run.export()
+        v = np.zeros(len(keys))
+        for kk, aa in zip(k, a):
+            v[index[O.key_int(kk)]] = aa
+        acc += v
+        acc2 += v * v
+    mean = acc / R
+    var = np.maximum(acc2 / R - mean ** 2, 0)
+    se = np.sqrt((var + np.abs(want)) / R)
+    touched = (var > 0) | (want != 0)
+    z = np.abs(mean - want)[touched] / se[touched]
+    assert np.all(z < 5.5), (np.max(z), np.argmax(z))
+    assert np.mean(z ** 2) < 1.5
+
+
+def test_early_compression_terms_and_no_compression_limit():
+    m = O.Model(O.REAL_1D, 8, 1, 8, 1.0, 2.0)
+    rng = np.random.default_rng(2)
+    basis = ED.basis_ints(ED.sparse_hamiltonian(m)[0])
+    sel = rng.choice(len(basis), 300, replace=False)
+    keys = [basis[i] for i in sel]
+    amps = (1.0 + rng.exponential(2.0, 300)) * rng.choice([-1, 1], 300)
+    # every spawn written under early compression is at least theta
+    run = O.Run(m, O.default_params(dt=0.01, compression=O.COMPRESS_EARLY))
+    run.seed(keys, amps, -1.0, step=5)
+    run.record_spawns()
+    run.step(1)
+    _, _, val = run.spawns()
+    assert len(val) > 0 and np.all(np.abs(val) >= 1.0)
+    late = O.Run(m, O.default_params(dt=0.01))
+    late.seed(keys, amps, -1.0, step=5)
+    late.record_spawns()
+    late.step(1)
+    assert len(late.spawns()[2]) > len(val)  # most small spawns are dropped
+    # with a threshold below every value nothing is compressed: early = late
+    tiny = dict(dt=0.01, threshold=2.0 ** -40)
+    a = O.Run(m, O.default_params(compression=O.COMPRESS_EARLY, **tiny))
+    b = O.Run(m, O.default_params(**tiny))
+    for r in (a, b):
+        r.seed(keys, amps, -1.0, step=5)
+        r.step(1)
+    (ka, va), (kb, vb) = a.export(), b.export()
+    assert np.array_equal(ka, kb) and np.array_equal(va, vb)
+    # the one-norm stays the exact sum although values below theta survive
+    e = O.Run(m, O.default_params(dt=0.01, compression=O.COMPRESS_EARLY))
+    e.seed(keys, amps, -1.0, step=5)
+    e.step(3)
+    k, v = e.export()
+    assert np.any(np.abs(v) < 1.0)
+    assert O.exact_norm(v, 1.0, O.MODE_REAL64) == e.state()[1]
