@@ -54,6 +54,7 @@ METRIC = "FCIQMC configs updated/s"
 UNIT = "configs/s"
 MODE_CODE = {"INT": 0, "REAL64": 1, "REAL32": 2, "DETERMINISTIC": 3}
 DTYPE = {"INT": "int64", "REAL64": "f64", "REAL32": "f32", "DETERMINISTIC": "f64"}
+ANN_CODE = {"auto": 0, "sort": 1, "hash": 2}
 # bytes fq_run_stats copies back per call: the error word and the run state
 STATS_D2H_BYTES = 4 + 192  # the error word, then the 192-byte run state
 KERNEL_FILES = ["fq_kernels.cuh", "fq_device.cuh", "fq_shared.h"]
@@ -327,7 +328,7 @@ def gpu_arm(args, cfg, name, dist, with_cpu=True):
     rank, world, local = dist_env()
     h = fq.Hamiltonian(cfg["kind"], cfg["Lx"], cfg["Ly"], cfg["N"], cfg["t"], cfg["u"])
     p = fq.default_params(mode=MODE_CODE[cfg["mode"]], dt=cfg["dt"], target=cfg["target"],
-                          seed=cfg["seed"], run_id=rank)
+                          seed=cfg["seed"], run_id=rank, annihilation=ANN_CODE[args.annihilation])
     run = fq.Run(h, p)
     run.seed_default(W.START_WEIGHT)
     equil = args.equil if args.equil is not None else cfg["steps"] // 4
@@ -391,6 +392,8 @@ def gpu_arm(args, cfg, name, dist, with_cpu=True):
     e2e_t = time.perf_counter() - t0
     e2e_value, _ = aggregate(dist, e2e_t, float(e2e_units))
     paths = run.merge_paths()
+    shape = run.shape()
+    arms = run.arm_times()
 
     out = None
     if rank == 0:
@@ -422,8 +425,9 @@ def gpu_arm(args, cfg, name, dist, with_cpu=True):
                        "graph_replay": True,
                        "l2": "working set per step %.2f GB > 129 MB L2; no flush" % (ws / 1e9),
                        "parallelism": "replicas x%d" % world,
-                       "launch_shape": run.shape(),
-                       "annihilation": "hash",
+                       "launch_shape": shape,
+                       "annihilation": shape["annihilation"],
+                       "autotuner_merge_ms_per_arm": arms,
                        "merge_buckets_onchip_scratch": list(paths)},
             "roofline": {"bound": "hbm", "kernel": "k_" + dom, "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -454,6 +458,8 @@ def brief(line):
             "len_mean": line["config"]["len_mean"], "spawns_mean": line["config"]["spawns_mean"],
             "kernel_ms": r["kernel_ms"], "kernel_gbs": r["kernel_gbs"],
             "kernel_frac": r["kernel_frac"], "dominant": r["kernel"], "frac": r["frac"],
+            "annihilation": line["config"]["annihilation"],
+            "autotuner_merge_ms_per_arm": line["config"]["autotuner_merge_ms_per_arm"],
             "clocks": line.get("clocks")}
 
 
@@ -628,6 +634,56 @@ def c3_precision_arm(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# c3 trajectories: FP32 against FP64 amplitudes over the configuration's 5000
+# steps at reduced targets, blocked energies where the population holds at
+# its target, and the full target's population over its first steps
+
+def c3_trajectory_arm(args):
+    import paper_2601_19505_gb300 as fq
+    from paper_2601_19505_gb300 import analysis as A
+
+    cfg = dict(W.CONFIGS["c3"])
+    out = {"workload": describe(cfg, "c3"), "runs": []}
+
+    def one(mode, target, steps):
+        h = fq.Hamiltonian(cfg["kind"], cfg["Lx"], cfg["Ly"], cfg["N"], cfg["t"], cfg["u"])
+        p = fq.default_params(mode=MODE_CODE[mode], dt=cfg["dt"], target=target, seed=cfg["seed"])
+        run = fq.Run(h, p)
+        run.seed_default(W.START_WEIGHT)
+        rows = []
+        t0 = time.perf_counter()
+        done = 0
+        while done < steps:
+            k = min(250, steps - done)
+            run.advance(k, chunk=k)
+            rows.append(run.history())
+            done += k
+        hist = np.concatenate(rows)
+        wall = time.perf_counter() - t0
+        run.close()
+        release_device_memory()
+        half = hist[len(hist) // 2:]
+        rec = {"mode": mode, "target": target, "steps": int(len(hist)), "wall_s": wall,
+               "norm_over_target_last_half": float(np.mean(half["norm"]) / target),
+               "len_max": int(hist["len"].max()), "step_of_len_max": int(hist["step"][np.argmax(hist["len"])]),
+               "trajectory_every_50": [[int(r["step"]), int(r["len"]), float(r["norm"]),
+                                        float(r["shift"])] for r in hist[::50]]}
+        sh = A.blocked_mean(half["shift"])
+        e = A.ratio_estimate(half["hproj"], half["vproj"])
+        rec["shift_last_half"] = [sh["mean"], sh["err"]]
+        rec["projected_last_half"] = [e["ratio"], e["err"]]
+        out["runs"].append(rec)
+        return rec
+
+    for target in (1e6, 1e7):
+        for mode in ("REAL32", "REAL64"):
+            one(mode, target, cfg["steps"])
+    one("REAL32", cfg["target"], args.steps)
+    print(json.dumps({"metric": METRIC + " (c3 trajectories)", "c3_trajectory": out}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -639,6 +695,8 @@ def main():
     ap.add_argument("--target", type=float, default=None,
                     help="override the workload's N_t (reduced cases for profiling)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--annihilation", choices=sorted(ANN_CODE), default="auto",
+                    help="annihilation arm (auto: the autotuner times hash and sort)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-more", action="store_true",
                     help="measure only the chosen workload (no nested c5-FP32, c2 and c4 lines)")
@@ -648,6 +706,9 @@ def main():
     ap.add_argument("--c3-precision", action="store_true",
                     help="c3: FP32 against FP64 amplitudes where the population first "
                          "reaches its target")
+    ap.add_argument("--c3-trajectory", action="store_true",
+                    help="c3: FP32 against FP64 trajectories over 5000 steps at N_t = 1e6 and "
+                         "1e7, and the first --steps steps at the configuration's N_t")
     ap.add_argument("--mode", choices=sorted(MODE_CODE), default=None,
                     help="the amplitude mode (default: FP64 for the c5 headline, else the "
                          "workload's own)")
@@ -676,6 +737,8 @@ def main():
         return 0
     if args.c3_precision:
         return c3_precision_arm(args)
+    if args.c3_trajectory:
+        return c3_trajectory_arm(args)
     dist = Dist(world, "nccl")
     out = gpu_arm(args, cfg, args.config, dist)
     if out is not None and world == 1 and headline and not args.no_more:

@@ -64,11 +64,15 @@ enum { FQ_BH_REAL_1D = 1, FQ_BH_REAL_2D = 2, FQ_BH_MOM_1D = 3 };
  * compression at all, the power iteration of Eq. fciqmc (FP64). */
 enum { FQ_MODE_INT = 0, FQ_MODE_REAL64 = 1, FQ_MODE_REAL32 = 2, FQ_MODE_DETERMINISTIC = 3 };
 
-/* Annihilation strategy (Sec. 6.3: summing spawns to one address).  HASH:
- * spawns are scattered into hash-segmented buckets and summed per address in
- * an on-chip open-addressing table.  SORT: the same buckets, sorted by
- * address and reduced by segment (not built yet: fq_run_create returns
- * FQ_ERR_INVALID).  AUTO picks HASH. */
+/* Annihilation strategy (Sec. 6.3: summing spawns to one address).  Both
+ * arms scatter spawns into hash-segmented buckets.  HASH: one warp sums a
+ * bucket's spawns per address in an open-addressing table in shared memory,
+ * then the segment's entries take their sums.  SORT: one warp sorts a
+ * bucket's contributions (the entries' diagonal terms, then the spawns) by a
+ * 16-bit hash of the address with a stable LSD radix sort of two 8-bit
+ * digits and sums each address's run (a segmented reduction).  Results are
+ * the same up to the order of FP sums.  AUTO: fq_run_autotune /
+ * fq_batch_autotune time both arms and keep the faster; HASH until then. */
 enum { FQ_ANN_AUTO = 0, FQ_ANN_SORT = 1, FQ_ANN_HASH = 2 };
 
 /* Where vector compression Pi acts (Sec. 7.1).  LATE (default, Eq.
@@ -269,18 +273,24 @@ int fq_run_merge_paths(fq_run *r, uint64_t *onchip, uint64_t *scratch);
  * candidate runs `steps` real steps, so the run advances. */
 int fq_run_autotune(fq_run *r, int steps);
 /* The launch shape the run steps with (after fq_run_autotune, the tuned
- * one): shape[0..5] = spawn warps per block, spawn blocks, merge warps per
- * block, merge blocks, on-chip table slots per merge warp, scratch table
- * slots per merge warp.  Needs a seeded run. */
+ * one): shape[0..6] = spawn warps per block, spawn blocks, merge warps per
+ * block, merge blocks, per merge warp the on-chip table slots (HASH) or
+ * sort-workspace elements (SORT) and the device-memory table slots or
+ * workspace elements for larger buckets, and the annihilation arm
+ * (FQ_ANN_HASH or FQ_ANN_SORT).  Needs a seeded run. */
 int fq_run_shape(fq_run *r, int *shape);
+/* The last fq_run_autotune's best mean merge-kernel time (ms) of each
+ * annihilation arm on the run's vector (0 for an arm it did not time). */
+int fq_run_arm_times(fq_run *r, float *hash_ms, float *sort_ms);
 /* Measurement: run n steps launched one kernel at a time (not from the graph)
  * with CUDA events around each kernel on the run's stream; ms[0], ms[1],
  * ms[2] = mean milliseconds per step of the spawning, merge and shift
  * kernels.  The run advances n steps (n <= 4096); synchronises. */
 int fq_run_profile(fq_run *r, int n, float *ms);
 
-/* A batch: B runs (same Hamiltonian kind, address width and mode; any sizes
- * and parameters) stepped together by one launch per kernel per step. */
+/* A batch: B runs (same Hamiltonian kind, address width, mode and
+ * annihilation strategy; any sizes and other parameters) stepped together by
+ * one launch per kernel per step. */
 int fq_batch_create(fq_batch **out, fq_run *const *runs, int B);
 void fq_batch_destroy(fq_batch *b);
 int fq_batch_step(fq_batch *b, int64_t n);

@@ -118,6 +118,7 @@ struct fq_run {
     bool has_tuned;
     unsigned scratch_slots;  // global scratch table size for buckets too big for SW
     unsigned forced_slots, forced_scratch;  // fq_run_set_tables overrides (0 = none)
+    unsigned sort_elems;   // global sort workspace per merge warp (elements)
     unsigned gen;  // bumped whenever a device pointer of the run changes
     unsigned last_err_bits;  // device error bits reported by the last check
     double* pinned;        // host staging slot for parameter updates
@@ -138,7 +139,10 @@ struct fq_batch {
     unsigned char* scratch;      // merge scratch tables (from runs[0]'s allocator)
     size_t scratch_bytes;
     unsigned scratch_ss;         // table size the scratch was last cleared for
+    unsigned char* sort_scratch;  // sort workspaces (from runs[0]'s allocator)
+    size_t sort_scratch_bytes;
     std::vector<LaunchCfg> shapes;  // launch shapes the scratch was sized for
+    float arm_ms[2];             // the autotuner's best mean merge time per arm (0: untimed)
     // replica overlaps (fq_batch_set_overlaps)
     bool ov_on;
     int ov_nq;
@@ -551,9 +555,11 @@ static cudaError_t sync_self(fq_run* r) {
 // a launch shape: persistent grids of one (spawn) or a few (merge) blocks per
 // SM, sized by occupancy; at most one warp per segment
 static LaunchCfg make_cfg(const KernelSet* ks, int spawn_var, int spawn_waves, int merge_var,
-                          unsigned slots, unsigned G) {
+                          unsigned slots, unsigned G, int ann) {
     LaunchCfg c;
+    memset(&c, 0, sizeof c);
     const int spawn_wpb = variant_wpb(spawn_var), merge_wpb = variant_wpb(merge_var);
+    c.ann = ann;
     c.spawn_var = spawn_var;
     c.spawn_wpb = spawn_wpb;
     c.merge_var = merge_var;
@@ -563,8 +569,8 @@ static LaunchCfg make_cfg(const KernelSet* ks, int spawn_var, int spawn_waves, i
     c.scratch = nullptr;
     const int sms = num_sms();
     int occ_s = ks->spawn_occupancy(spawn_var);
-    const size_t smem = (size_t)merge_wpb * slots * ks->slot_bytes;
-    int occ_m = ks->merge_occupancy(merge_var, smem);
+    const size_t smem = ks->merge_smem(ann, merge_wpb, slots);
+    int occ_m = ks->merge_occupancy(ann, merge_var, smem);
     if (occ_s < 1) occ_s = 1;
     if (occ_m < 1) occ_m = 1;
     const long long ws = ((long long)G + spawn_wpb - 1) / spawn_wpb;
@@ -591,6 +597,10 @@ static void table_sizes(fq_run* r) {
         r->forced_scratch
             ? r->forced_scratch
             : std::max(r->slots, next_pow2((unsigned long long)std::ceil((r->Cv + r->Cs) / 0.9)));
+    // the sort arm's workspace holds a bucket's entries and spawns (16-bit
+    // indices: at most 32768 elements; a larger bucket fails the step)
+    r->sort_elems = (unsigned)std::min<unsigned long long>(
+        32768, next_pow2((unsigned long long)r->Cv + r->Cs));
 }
 
 // per-segment capacities for totals lcap, scap over B segments (spawns
@@ -613,7 +623,9 @@ extern "C" int fq_run_create(fq_run** out, const fq_ham* h, const fq_params* p, 
     if (p->mode < FQ_MODE_INT || p->mode > FQ_MODE_DETERMINISTIC) return FQ_ERR_INVALID;
     if (p->mode != FQ_MODE_DETERMINISTIC && p->mode != FQ_MODE_INT && !(p->threshold > 0))
         return FQ_ERR_INVALID;
-    if (p->annihilation != FQ_ANN_AUTO && p->annihilation != FQ_ANN_HASH) return FQ_ERR_INVALID;
+    if (p->annihilation != FQ_ANN_AUTO && p->annihilation != FQ_ANN_HASH &&
+        p->annihilation != FQ_ANN_SORT)
+        return FQ_ERR_INVALID;
     if (p->compression != FQ_COMPRESS_LATE && p->compression != FQ_COMPRESS_EARLY)
         return FQ_ERR_INVALID;
     if (p->mode == FQ_MODE_INT && p->target > 1e12) return FQ_ERR_INVALID;
@@ -1085,10 +1097,15 @@ static void batch_free(fq_batch* b) {
     if (!b) return;
     batch_release(b);
     overlaps_free(b);
+    fq_run* r0 = b->runs[0];
     if (b->scratch) {
-        fq_run* r0 = b->runs[0];
         if (r0->has_alloc) r0->alloc.free(r0->alloc.ctx, b->scratch, b->scratch_bytes, (void*)r0->stream);
         else cudaFreeAsync(b->scratch, r0->stream);
+    }
+    if (b->sort_scratch) {
+        if (r0->has_alloc)
+            r0->alloc.free(r0->alloc.ctx, b->sort_scratch, b->sort_scratch_bytes, (void*)r0->stream);
+        else cudaFreeAsync(b->sort_scratch, r0->stream);
     }
     delete b;
 }
@@ -1110,17 +1127,27 @@ static int capture(fq_batch* b, int n, cudaGraphExec_t* out) {
 
 // the launch shapes a batch may use: the default first, then the ones the
 // autotuner tries
+// the annihilation arms a batch may use: the runs' choice, both for AUTO
+static std::vector<int> batch_arms(const fq_batch* b) {
+    const int a = b->runs[0]->prm.annihilation;
+    if (a == FQ_ANN_HASH) return {FQ_ANN_HASH_ARM};
+    if (a == FQ_ANN_SORT) return {FQ_ANN_SORT_ARM};
+    return {FQ_ANN_HASH_ARM, FQ_ANN_SORT_ARM};
+}
+
 static std::vector<LaunchCfg> batch_shapes(fq_batch* b, unsigned slots) {
     std::vector<LaunchCfg> v;
     const size_t limit = 200u * 1024u;
-    v.push_back(make_cfg(b->ks, 0, 1, 0, slots, b->G));
-    for (int sv = 0; sv < kKernelVariants; ++sv)
-        for (int waves : {1, 2})
-            for (int mv = 0; mv < kKernelVariants; ++mv)
-                for (unsigned sl : {slots / 2, slots, slots * 2}) {
-                    if (sl < 64 || (size_t)variant_wpb(mv) * sl * b->ks->slot_bytes > limit) continue;
-                    v.push_back(make_cfg(b->ks, sv, waves, mv, sl, b->G));
-                }
+    const std::vector<int> arms = batch_arms(b);
+    v.push_back(make_cfg(b->ks, 0, 1, 0, slots, b->G, arms[0]));
+    for (int ann : arms)
+        for (int sv = 0; sv < kKernelVariants; ++sv)
+            for (int waves : {1, 2})
+                for (int mv = 0; mv < kKernelVariants; ++mv)
+                    for (unsigned sl : {slots / 2, slots, slots * 2}) {
+                        if (sl < 64 || b->ks->merge_smem(ann, variant_wpb(mv), sl) > limit) continue;
+                        v.push_back(make_cfg(b->ks, sv, waves, mv, sl, b->G, ann));
+                    }
     return v;
 }
 
@@ -1130,7 +1157,7 @@ static int batch_build(fq_batch* b) {
     for (size_t i = 0; i < nr; ++i) b->gens[i] = b->runs[i]->gen;
     std::vector<RunDesc> desc(nr);
     std::vector<unsigned> seg_run;
-    unsigned base = 0, slots = 0, ss = 0;
+    unsigned base = 0, slots = 0, ss = 0, se = 0;
     for (size_t i = 0; i < nr; ++i) {
         fq_run* r = b->runs[i];
         fill_desc(r, desc[i], base);
@@ -1138,6 +1165,7 @@ static int batch_build(fq_batch* b) {
         base += r->B;
         slots = std::max(slots, r->slots);
         ss = std::max(ss, r->scratch_slots);
+        se = std::max(se, r->sort_elems);
     }
     b->G = base;
     CK(cudaMalloc((void**)&b->d_desc, sizeof(RunDesc) * nr));
@@ -1170,9 +1198,33 @@ static int batch_build(fq_batch* b) {
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(r0->stream));
     }
+    // sort workspaces in device memory, when a sort shape may run (no
+    // clearing needed: each use writes before it reads)
+    bool sort_shapes = false;
+    for (const LaunchCfg& c : b->shapes) sort_shapes |= c.ann == FQ_ANN_SORT_ARM;
+    const size_t sbytes = sort_shapes ? warps * b->ks->sort_ws_bytes(se) : 0;
+    if (sbytes > b->sort_scratch_bytes) {
+        fq_run* r0 = b->runs[0];
+        if (b->sort_scratch) {
+            CK(cudaStreamSynchronize(b->stream));
+            if (r0->has_alloc)
+                r0->alloc.free(r0->alloc.ctx, b->sort_scratch, b->sort_scratch_bytes, (void*)r0->stream);
+            else cudaFreeAsync(b->sort_scratch, r0->stream);
+            b->sort_scratch = nullptr;
+            b->sort_scratch_bytes = 0;
+        }
+        void* p = nullptr;
+        if (r0->has_alloc) p = r0->alloc.alloc(r0->alloc.ctx, sbytes, (void*)r0->stream);
+        else if (cudaMallocAsync(&p, sbytes, r0->stream) != cudaSuccess) p = nullptr;
+        if (!p) return FQ_ERR_NOMEM;
+        b->sort_scratch = (unsigned char*)p;
+        b->sort_scratch_bytes = sbytes;
+    }
     for (LaunchCfg& c : b->shapes) {
         c.scratch = b->scratch;
         c.scratch_slots = ss;
+        c.sort_scratch = b->sort_scratch;
+        c.sort_elems = se;
     }
     {
         const int rc = overlaps_build(b);
@@ -1183,7 +1235,8 @@ static int batch_build(fq_batch* b) {
         const LaunchCfg& t = b->runs[0]->tuned;
         for (const LaunchCfg& c : b->shapes)
             if (c.spawn_var == t.spawn_var && c.spawn_grid == t.spawn_grid &&
-                c.merge_var == t.merge_var && c.merge_grid == t.merge_grid && c.slots == t.slots)
+                c.merge_var == t.merge_var && c.merge_grid == t.merge_grid && c.slots == t.slots &&
+                c.ann == t.ann)
                 b->cfg = c;
     }
     int rc = capture(b, 1, &b->g1);
@@ -1595,7 +1648,8 @@ static int autotune(fq_batch* b, int steps) {
         bool seen_s = false, seen_m = false;
         for (const LaunchCfg& x : sc) seen_s |= x.spawn_var == c.spawn_var && x.spawn_grid == c.spawn_grid;
         for (const LaunchCfg& x : mc)
-            seen_m |= x.merge_var == c.merge_var && x.merge_grid == c.merge_grid && x.slots == c.slots;
+            seen_m |= x.merge_var == c.merge_var && x.merge_grid == c.merge_grid &&
+                      x.slots == c.slots && x.ann == c.ann;
         if (!seen_s) sc.push_back(c);
         if (!seen_m) mc.push_back(c);
     }
@@ -1645,6 +1699,12 @@ static int autotune(fq_batch* b, int steps) {
         if (ts[i] / ns[i] < ts[bs] / ns[bs]) bs = i;
     for (size_t i = 1; i < mc.size(); ++i)
         if (tm[i] / nm[i] < tm[bm] / nm[bm]) bm = i;
+    b->arm_ms[0] = b->arm_ms[1] = 0.0f;
+    for (size_t i = 0; i < mc.size(); ++i) {
+        float& a = b->arm_ms[mc[i].ann == FQ_ANN_SORT_ARM ? 1 : 0];
+        const float t = (float)(tm[i] / nm[i]);
+        if (a == 0.0f || t < a) a = t;
+    }
     LaunchCfg best = mc[bm];
     best.spawn_var = sc[bs].spawn_var;
     best.spawn_wpb = sc[bs].spawn_wpb;
@@ -1670,6 +1730,13 @@ extern "C" int fq_run_autotune(fq_run* r, int steps) {
     return run_check(r);
 }
 
+extern "C" int fq_run_arm_times(fq_run* r, float* hash_ms, float* sort_ms) {
+    if (!r || !hash_ms || !sort_ms) return FQ_ERR_INVALID;
+    *hash_ms = r->single ? r->single->arm_ms[0] : 0.0f;
+    *sort_ms = r->single ? r->single->arm_ms[1] : 0.0f;
+    return FQ_OK;
+}
+
 extern "C" int fq_run_shape(fq_run* r, int* shape) {
     if (!r || !shape || !r->seeded) return FQ_ERR_INVALID;
     int rc = single_batch(r);
@@ -1681,7 +1748,8 @@ extern "C" int fq_run_shape(fq_run* r, int* shape) {
     shape[2] = c.merge_wpb;
     shape[3] = c.merge_grid;
     shape[4] = (int)c.slots;
-    shape[5] = (int)c.scratch_slots;
+    shape[5] = (int)(c.ann == FQ_ANN_SORT_ARM ? c.sort_elems : c.scratch_slots);
+    shape[6] = c.ann == FQ_ANN_SORT_ARM ? FQ_ANN_SORT : FQ_ANN_HASH;
     return FQ_OK;
 }
 
@@ -1726,7 +1794,9 @@ extern "C" int fq_batch_create(fq_batch** out, fq_run* const* runs, int B) {
     *out = nullptr;
     for (int i = 0; i < B; ++i) {
         if (!runs[i] || !runs[i]->seeded) return FQ_ERR_INVALID;
-        if (runs[i]->ks != runs[0]->ks || runs[i]->stream != runs[0]->stream) return FQ_ERR_INVALID;
+        if (runs[i]->ks != runs[0]->ks || runs[i]->stream != runs[0]->stream ||
+            runs[i]->prm.annihilation != runs[0]->prm.annihilation)
+            return FQ_ERR_INVALID;
         for (int j = 0; j < i; ++j)
             if (runs[j] == runs[i]) return FQ_ERR_INVALID;
     }

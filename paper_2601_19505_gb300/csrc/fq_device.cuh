@@ -127,6 +127,40 @@ template <class K> __device__ __forceinline__ K add_boson(K k, int s) {
 // bits that start a run of ones: one per occupied mode
 template <class K> __device__ __forceinline__ K run_starts(K k) { return k & ~(k << 1); }
 
+// bits [p, p + 64) of x (0 above the top), and bits [p - 64, p) with bit
+// p - 1 at the top (0 below bit 0); 0 <= p <= W
+__device__ __forceinline__ uint64_t window_up(uint64_t x, int p) { return p >= 64 ? 0ull : x >> p; }
+__device__ __forceinline__ uint64_t window_up(u128 x, int p) {
+    return p >= 128 ? 0ull : (uint64_t)(x >> p);
+}
+__device__ __forceinline__ uint64_t window_down(uint64_t x, int p) {
+    return p <= 0 ? 0ull : x << (64 - p);
+}
+__device__ __forceinline__ uint64_t window_down(u128 x, int p) {
+    return p <= 0 ? 0ull : (uint64_t)((x << (128 - p)) >> 64);
+}
+
+// start bit of mode s2 of address k, given the start P of an occupied mode
+// s != s2.  Counting separators from P: for s2 > s, separator s2 - 1 is the
+// (s2 - s)-th zero at or above P; for s2 < s, it is the (s - s2 + 1)-th zero
+// below P.  Found in one 64-bit window around P when it holds that many
+// zeros (always, unless over 50-odd bosons sit between the two modes), else
+// by the search from bit 0.  Zeros past either end of the address are never
+// reached first: the separator sought lies inside it.
+template <class K> __device__ __forceinline__ int mode_start_from(K k, int P, int s, int s2) {
+    if (s2 > s) {
+        const uint64_t z = ~window_up(k, P);
+        const int j = s2 - s;
+        if (__popcll(z) >= j) return P + nth_set64(z, j - 1) + 1;
+    } else {
+        if (s2 == 0) return 0;
+        const uint64_t z = __brevll(~window_down(k, P));  // bit t = bit P - 1 - t
+        const int j = s - s2 + 1;
+        if (__popcll(z) >= j) return P - nth_set64(z, j - 1);
+    }
+    return mode_start(k, s2);
+}
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and the draw layout:
 //   key     = (seed_lo32, seed_hi32 ^ run_id * 0x9E3779B9)
@@ -167,20 +201,12 @@ __device__ __forceinline__ unsigned pick(uint4 w, unsigned m) {
 // multiply by an odd constant (multiplicative hashing), unrelated to the
 // golden-ratio constant of the merge table's slot hash (with related
 // constants, small addresses that share a segment would also share a few
-// table slots).  128-bit addresses (h already folds the high word through
-// splitmix64): the murmur3 64-bit finaliser (Appleby), which measured faster
-// for them.
-__device__ __forceinline__ uint64_t fmix64(uint64_t h) {
-    h ^= h >> 33;
-    h *= 0xFF51AFD7ED558CCDull;
-    h ^= h >> 33;
-    h *= 0xC4CEB9FE1A85EC53ull;
-    h ^= h >> 33;
-    return h;
-}
-template <class K> __device__ __forceinline__ uint64_t seg_mix(uint64_t h) {
-    if constexpr (sizeof(K) == 8) return h * 0xD6E8FEB86659FD93ull;
-    else return fmix64(h);
+// table slots).
+// 128-bit addresses fold the high word in by a multiply with another odd
+// constant, then take the same multiply: two 64-bit multiplies in all.
+__device__ __forceinline__ uint64_t seg_hash(uint64_t k) { return k * 0xD6E8FEB86659FD93ull; }
+__device__ __forceinline__ uint64_t seg_hash(u128 k) {
+    return ((uint64_t)k ^ ((uint64_t)(k >> 64) * 0xC2B2AE3D27D4EB4Full)) * 0xD6E8FEB86659FD93ull;
 }
 __device__ __forceinline__ unsigned segment_of(uint64_t mixed, int log2B) {
     return log2B ? (unsigned)(mixed >> (64 - log2B)) : 0u;
@@ -261,24 +287,58 @@ template <int KIND> struct RealModel {
             else val = __ldg(p.hop_tab + ns * (nt + 1));
             return dest;
         }
-        // 2D: the neighbouring site from the model's table; a hop to the
-        // next or previous site moves one separator (as in 1D), any other
-        // removes a one-bit at P and inserts one at the start of the target
-        // run, located once
+        // 2D: the neighbouring site s2 from the model's table.  Every
+        // direction takes one path (no divergence within a warp): the
+        // target run's start q is found by counting separators from P inside
+        // one 64-bit window of the address, and only the bits between the
+        // two runs change -- moving a boson from site s to a later site
+        // shifts bits [P, q) down by one and sets bit q - 1; to an earlier
+        // site it shifts bits [q, P] up by one and sets bit q.  Targets
+        // beyond the window take the search from bit 0.
         typedef KeyOps<K> O;
         const int s = P - O::popc(key & O::low(P));
-        const int ns = run_from(key, P);
         const int s2 = p.nbr[d][s];
-        int nt;
-        K dest;
-        if (s2 == s + 1) {
-            nt = run_from(key, P + ns + 1);
-            dest = key ^ ((K)3 << (P + ns - 1));
-        } else if (s2 == s - 1) {
-            const K z = ~key & O::low(P - 1);
-            nt = z ? (P - 2 - (O::W - 1 - clz_k(z))) : (P - 1);
-            dest = key ^ ((K)3 << (P - 1));
-        } else {
+        const uint64_t wu = window_up(key, P);  // bit i = bit P + i
+        int ns = -1, nt = -1;
+        K dest = key;
+        if (~wu) {
+            ns = __ffsll((long long)~wu) - 1;
+            if (s2 > s) {
+                const uint64_t z = ~wu;
+                const int j = s2 - s;
+                const int L = __popcll(z) >= j ? nth_set64(z, j - 1) + 1 : 64;  // q - P
+                if (L < 64) {
+                    const uint64_t up = wu >> L;             // bit i = bit q + i
+                    const int r2 = __ffsll((long long)~up) - 1;
+                    if (L + r2 < 64) {                       // the target run ends inside
+                        nt = r2;
+                        const uint64_t w = wu & ((1ull << L) - 1ull);
+                        const uint64_t nw = (w >> 1) | (1ull << (L - 1));
+                        dest = key ^ O::shl((K)(w ^ nw), P);
+                    }
+                }
+            } else if (s2 > 0) {
+                const uint64_t wd = window_down(key, P);  // bit 63 = bit P - 1
+                const uint64_t z = __brevll(~wd);         // bit t = zero at P - 1 - t
+                const int j = s - s2 + 1;
+                if (__popcll(z) >= j) {
+                    const int t = nth_set64(z, j - 1);    // t >= 1: q = P - t
+                    const uint64_t below = wd >> (64 - t);  // bits q .. P - 1
+                    nt = __ffsll((long long)~below) - 1;
+                    const uint64_t w = below | (1ull << t);  // bits q .. P
+                    const uint64_t nw = ((w << 1) | 1ull) & (t == 63 ? ~0ull : ((2ull << t) - 1ull));
+                    dest = key ^ O::shl((K)(w ^ nw), P - t);
+                }
+            } else if (P < 63) {  // to site 0: q = 0, bits 0 .. P
+                const uint64_t below = window_down(key, P) >> (64 - P);  // bits 0 .. P - 1 (P >= 1)
+                nt = __ffsll((long long)~below) - 1;
+                const uint64_t w = below | (1ull << P);
+                const uint64_t nw = ((w << 1) | 1ull) & ((2ull << P) - 1ull);
+                dest = key ^ (K)(w ^ nw);
+            }
+        }
+        if (nt < 0) {  // the search from bit 0
+            ns = run_from(key, P);
             const int q = mode_start(key, s2);
             nt = run_from(key, q);
             dest = ins_one(del_bit(key, P), q - (s2 > s ? 1 : 0));

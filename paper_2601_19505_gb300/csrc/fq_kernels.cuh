@@ -18,7 +18,7 @@
 //
 // Layout: the vector of a run is hash-segmented (the paper's PDVec segments,
 // Sec. 6.4, as thousands of small segments sized for one merge warp's
-// on-chip table): segment b = top log2(B) bits of seg_mix(h(address)), capacity Cv
+// on-chip table): segment b = top log2(B) bits of seg_hash(address), capacity Cv
 // entries each, structure-of-arrays keys/amplitudes.  Spawn buckets use the
 // same segment map with capacity Cs.  All sizes and pointers are read from
 // device memory, so one captured CUDA graph replays any number of steps.
@@ -303,7 +303,7 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     auto emit = [&](bool has, K dest, S val) {
         unsigned bk = 0, pos = 0;
         if (has) {
-            bk = segment_of(seg_mix<K>(KeyOps<K>::rng_h(dest)), log2B);
+            bk = segment_of(seg_hash(dest), log2B);
             pos = atomicAdd(&sfill[bk], 1u);
             ++n_sp;
         }
@@ -660,6 +660,85 @@ __device__ __forceinline__ void merge_emit(const RunDesc* R, bool has, K key,
     nout += (unsigned)__popc(bal);
 }
 
+// The end of a bucket: the projected-energy terms whose address falls in it
+// (the survivors read back: this warp wrote them), the new segment's count,
+// and the bucket's spawn counter cleared for the next step.
+template <class K, int AMP>
+__device__ __forceinline__ void bucket_finish(const RunDesc* R, unsigned seg, unsigned cur,
+                                              unsigned nout, const K* ok,
+                                              const typename AmpT<AMP>::A* oa, int lane) {
+    const unsigned Cv = R->Cv;
+    const unsigned e0 = R->ref_off[seg], e1 = R->ref_off[seg + 1];
+    if (e1 > e0) {  // warp-uniform
+        const K* rk = (const K*)R->ref_keys;
+        const unsigned nw = nout <= Cv ? nout : Cv;
+        double hp = 0.0, vp = 0.0;
+        for (unsigned e = e0; e < e1; ++e) {
+            const K want = rk[e];
+            double cv = 0.0;
+            for (unsigned i = lane; i < nw; i += 32)
+                if (ok[i] == want) cv = (double)oa[i];
+            cv = warp_sum(cv);  // at most one lane holds the address
+            hp += R->ref_h[e] * cv;
+            vp += R->ref_v[e] * cv;
+        }
+        if (lane == 0) {
+            R->part_h[seg] = hp;
+            R->part_v[seg] = vp;
+        }
+    }
+    if (lane == 0) {
+        R->vcount[cur ^ 1][seg] = nout <= Cv ? nout : Cv;
+        R->sfill[seg] = 0u;
+    }
+}
+
+// The diagonal term of an entry c of c^(n) at `key`: c (1 + dt (S - H_ii))
+// (Eq. stochasticTransitionOperator; integer walkers round it stochastically
+// with the draw of stream 0xFFFFFFFE); under early compression it is then
+// compressed alone with the draw of stream 0xFFFFFFFD (0 when dropped).
+template <class K, int AMP, int KIND>
+__device__ __forceinline__ typename AmpT<AMP>::ACC diag_term(const RunDesc* R, K key,
+                                                            typename AmpT<AMP>::A c, uint2 rkey,
+                                                            unsigned stepno, int early) {
+    typedef typename AmpT<AMP>::ACC ACC;
+    typedef Model<KIND> MD;
+    ACC w;
+    if constexpr (KIND != FQ_KIND_MOM_1D) {
+        const int si = MD::diag_index(key);
+        if constexpr (AMP == FQ_AMP_F32) {
+            w = c + c * __ldg(R->del32 + si);
+        } else if constexpr (AMP == FQ_AMP_F64) {
+            w = c * __ldg(R->fac64 + si);
+        } else {
+            const double x = (double)c * __ldg(R->fac64 + si);
+            const double fl = floor(x);
+            const uint4 r4 = draw(rkey, stepno, 0xFFFFFFFEu, KeyOps<K>::rng_h(key));
+            w = (ACC)((long long)fl + (uniform53(r4) < x - fl ? 1 : 0));
+        }
+    } else {
+        const double hii = MD::diagonal(R->mp, key);
+        const double S0 = R->st->shift, dt = R->st->dt;
+        if constexpr (AMP == FQ_AMP_F32) {
+            w = c + c * (float)(dt * (S0 - hii));
+        } else if constexpr (AMP == FQ_AMP_F64) {
+            w = c * (1.0 + dt * (S0 - hii));
+        } else {
+            const double x = (double)c * (1.0 + dt * (S0 - hii));
+            const double fl = floor(x);
+            const uint4 r4 = draw(rkey, stepno, 0xFFFFFFFEu, KeyOps<K>::rng_h(key));
+            w = (ACC)((long long)fl + (uniform53(r4) < x - fl ? 1 : 0));
+        }
+    }
+    if constexpr (AMP != FQ_AMP_INT) {
+        if (early && !at_least_theta(w, R)) {
+            const uint4 r4 = draw(rkey, stepno, 0xFFFFFFFDu, KeyOps<K>::rng_h(key));
+            if (!pi_below(w, r4, R)) w = (ACC)0;
+        }
+    }
+    return w;
+}
+
 // One bucket.  The spawns go into the table (tk, ta, tl; mask + 1 slots, all
 // EMPTY / 0 on entry and on return), which sums them per address.  Then each
 // entry of c^(n)'s segment, with its diagonal term, takes over the sum of
@@ -746,40 +825,7 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
             ACC w = (ACC)0;
             const bool has = i < n_old;
             if (has) {
-                if constexpr (KIND != FQ_KIND_MOM_1D) {
-                    const int si = MD::diag_index(key);
-                    if constexpr (AMP == FQ_AMP_F32) {
-                        w = c + c * __ldg(R->del32 + si);
-                    } else if constexpr (AMP == FQ_AMP_F64) {
-                        w = c * __ldg(R->fac64 + si);
-                    } else {
-                        const double x = (double)c * __ldg(R->fac64 + si);
-                        const double fl = floor(x);
-                        const uint4 r4 = draw(rkey, stepno, 0xFFFFFFFEu, KeyOps<K>::rng_h(key));
-                        w = (ACC)((long long)fl + (uniform53(r4) < x - fl ? 1 : 0));
-                    }
-                } else {
-                    const double hii = MD::diagonal(R->mp, key);
-                    const double S0 = R->st->shift, dt = R->st->dt;
-                    if constexpr (AMP == FQ_AMP_F32) {
-                        w = c + c * (float)(dt * (S0 - hii));
-                    } else if constexpr (AMP == FQ_AMP_F64) {
-                        w = c * (1.0 + dt * (S0 - hii));
-                    } else {
-                        const double x = (double)c * (1.0 + dt * (S0 - hii));
-                        const double fl = floor(x);
-                        const uint4 r4 = draw(rkey, stepno, 0xFFFFFFFEu, KeyOps<K>::rng_h(key));
-                        w = (ACC)((long long)fl + (uniform53(r4) < x - fl ? 1 : 0));
-                    }
-                }
-                if constexpr (AMP != FQ_AMP_INT) {
-                    // early compression: the diagonal term alone, with the
-                    // draw of stream 0xFFFFFFFD of its address
-                    if (early && !at_least_theta(w, R)) {
-                        const uint4 r4 = draw(rkey, stepno, 0xFFFFFFFDu, KeyOps<K>::rng_h(key));
-                        if (!pi_below(w, r4, R)) w = (ACC)0;
-                    }
-                }
+                w = diag_term<K, AMP, KIND>(R, key, c, rkey, stepno, early);
                 if (n_sp) {
                     const int q = table_find(tk, mask, key);
                     if (q >= 0) {
@@ -809,37 +855,157 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
                               acc);
     }
     __syncwarp();
-    // projected-energy terms whose address falls in this bucket: read the
-    // survivors back (this warp wrote them)
-    const unsigned e0 = R->ref_off[seg], e1 = R->ref_off[seg + 1];
-    if (e1 > e0) {  // warp-uniform
-        const K* rk = (const K*)R->ref_keys;
-        const unsigned nw = nout <= Cv ? nout : Cv;
-        double hp = 0.0, vp = 0.0;
-        for (unsigned e = e0; e < e1; ++e) {
-            const K want = rk[e];
-            double cv = 0.0;
-            for (unsigned i = lane; i < nw; i += 32)
-                if (ok[i] == want) cv = (double)oa[i];
-            cv = warp_sum(cv);  // at most one lane holds the address
-            hp += R->ref_h[e] * cv;
-            vp += R->ref_v[e] * cv;
-        }
-        if (lane == 0) {
-            R->part_h[seg] = hp;
-            R->part_v[seg] = vp;
-        }
-    }
+    bucket_finish<K, AMP>(R, seg, cur, nout, ok, oa, lane);
     // release the used slots for the next bucket
     for (unsigned i = lane; i < nl; i += 32) {
         const unsigned q = tl[i];
         tk[q] = EMPTY;
         ta[q] = (ACC)0;
     }
-    if (lane == 0) {
-        R->vcount[cur ^ 1][seg] = nout <= Cv ? nout : Cv;
-        R->sfill[seg] = 0u;
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// Annihilation by sorting (FQ_ANN_SORT).  A bucket's contributions -- the
+// diagonal terms of c^(n)'s segment first, then the spawns in arrival order --
+// are sorted by a 16-bit hash of their address with a stable LSD radix sort of
+// two 8-bit digits: digit counts, their exclusive scan, then a scatter in
+// rounds of 32 that ranks a round's equal digits by __match_any_sync.  Every
+// address's contributions then lie in one run of equal hash, in their original
+// order; the first occurrence of each address in its run sums the run's
+// contributions to that address (a segmented reduction), and Pi, compaction
+// and the norm terms follow as in the hash arm.  The address set and every
+// decision are the hash arm's; FP sums differ only in their order.
+
+// per-warp workspace of C elements: address, value, 16-bit hash and two
+// 16-bit index arrays, then 256 digit counters
+template <class K, int AMP> struct SortWs {
+    typedef typename AmpT<AMP>::ACC ACC;
+    static constexpr size_t al(size_t b) { return (b + 15) / 16 * 16; }
+    __host__ __device__ static constexpr size_t val_off(unsigned C) { return al((size_t)C * sizeof(K)); }
+    __host__ __device__ static constexpr size_t hash_off(unsigned C) {
+        return val_off(C) + al((size_t)C * sizeof(ACC));
     }
+    __host__ __device__ static constexpr size_t ia_off(unsigned C) { return hash_off(C) + al((size_t)C * 2); }
+    __host__ __device__ static constexpr size_t ib_off(unsigned C) { return ia_off(C) + al((size_t)C * 2); }
+    __host__ __device__ static constexpr size_t bins_off(unsigned C) { return ib_off(C) + al((size_t)C * 2); }
+    __host__ __device__ static constexpr size_t bytes(unsigned C) { return bins_off(C) + 256 * 4; }
+};
+
+template <class K> __device__ __forceinline__ unsigned short hash16(K key) {
+    return (unsigned short)((fold32(key) * 0x9E3779B1u) >> 16);
+}
+
+template <class K, int AMP, int KIND>
+__device__ __forceinline__ void sort_bucket(const RunDesc* R, unsigned seg, unsigned cur,
+                                            unsigned n_old, unsigned n_sp, unsigned char* ws,
+                                            unsigned C, int lane, MergeAcc& acc) {
+    typedef typename AmpT<AMP>::A A;
+    typedef typename AmpT<AMP>::S S;
+    typedef typename AmpT<AMP>::ACC ACC;
+    typedef SortWs<K, AMP> L;
+    const K EMPTY = KeyOps<K>::empty();
+    const unsigned Cv = R->Cv;
+    const K* __restrict__ vk = (const K*)R->vkeys[cur] + (size_t)seg * Cv;
+    const A* __restrict__ va = (const A*)R->vamps[cur] + (size_t)seg * Cv;
+    K* __restrict__ ok = (K*)R->vkeys[cur ^ 1] + (size_t)seg * Cv;
+    A* __restrict__ oa = (A*)R->vamps[cur ^ 1] + (size_t)seg * Cv;
+    const K* __restrict__ sk = (const K*)R->skeys + (size_t)seg * R->Cs;
+    const S* __restrict__ sv = (const S*)R->samps + (size_t)seg * R->Cs;
+    const unsigned stepno = (unsigned)(R->st->step + 1);
+    const uint2 rkey = make_uint2(R->key_x, R->key_y);
+    const int nq = R->norm_q, det = R->mode_det, early = R->early;
+    K* const wk = (K*)ws;
+    ACC* const wv = (ACC*)(ws + L::val_off(C));
+    unsigned short* const wh = (unsigned short*)(ws + L::hash_off(C));
+    unsigned short* const ia = (unsigned short*)(ws + L::ia_off(C));
+    unsigned short* const ib = (unsigned short*)(ws + L::ib_off(C));
+    unsigned* const bins = (unsigned*)(ws + L::bins_off(C));
+    const unsigned n = n_old + n_sp;
+
+    for (unsigned i = lane; i < n_old; i += 32) {
+        const K key = vk[i];
+        wk[i] = key;
+        wv[i] = diag_term<K, AMP, KIND>(R, key, va[i], rkey, stepno, early);
+        wh[i] = hash16(key);
+        ia[i] = (unsigned short)i;
+    }
+    for (unsigned j = lane; j < n_sp; j += 32) {
+        const K key = sk[j];
+        const unsigned i = n_old + j;
+        wk[i] = key;
+        wv[i] = (ACC)sv[j];
+        wh[i] = hash16(key);
+        ia[i] = (unsigned short)i;
+    }
+    __syncwarp();
+    for (int pass = 0; pass < 2; ++pass) {
+        const int shift = 8 * pass;
+        const unsigned short* src = pass ? ib : ia;
+        unsigned short* dst = pass ? ia : ib;
+        for (unsigned b = lane; b < 256; b += 32) bins[b] = 0u;
+        __syncwarp();
+        for (unsigned i = lane; i < n; i += 32) atomicAdd(&bins[(wh[src[i]] >> shift) & 255u], 1u);
+        __syncwarp();
+        unsigned v[8], t = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            v[k] = bins[8 * lane + k];
+            t += v[k];
+        }
+        unsigned run = warp_incl_scan(t, lane) - t;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            bins[8 * lane + k] = run;
+            run += v[k];
+        }
+        __syncwarp();
+        for (unsigned i0 = 0; i0 < n; i0 += 32) {
+            const unsigned i = i0 + lane;
+            const bool valid = i < n;
+            const unsigned e = valid ? src[i] : 0u;
+            const unsigned d = valid ? ((unsigned)(wh[e] >> shift) & 255u) : 256u + (unsigned)lane;
+            const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+            if (valid) dst[bins[d] + __popc(peers & ((1u << lane) - 1u))] = (unsigned short)e;
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) bins[d] += (unsigned)__popc(peers);
+            __syncwarp();
+        }
+    }
+    // sorted order in ia; each address's first position in its hash run sums
+    unsigned nout = 0;
+    for (unsigned i0 = 0; i0 < n; i0 += 32) {
+        const unsigned i = i0 + lane;
+        bool head = false;
+        ACC w = (ACC)0;
+        K key = EMPTY;
+        if (i < n) {
+            const unsigned e = ia[i];
+            key = wk[e];
+            const unsigned short h = wh[e];
+            head = true;
+            for (unsigned j = i; j > 0;) {
+                const unsigned f = ia[--j];
+                if (wh[f] != h) break;
+                if (wk[f] == key) {
+                    head = false;
+                    break;
+                }
+            }
+            if (head) {
+                w = wv[e];
+                for (unsigned j = i + 1; j < n; ++j) {
+                    const unsigned f = ia[j];
+                    if (wh[f] != h) break;
+                    if (wk[f] == key) w = w + wv[f];
+                }
+            }
+        }
+        merge_emit<K, AMP>(R, head, key, w, rkey, stepno, ok, oa, Cv, nq, det, early, lane, nout,
+                           acc);
+    }
+    __syncwarp();
+    bucket_finish<K, AMP>(R, seg, cur, nout, ok, oa, lane);
     __syncwarp();
 }
 
@@ -850,7 +1016,13 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
 //     whose spawns could exceed 0.7 SW uses the warp's table of SS slots in
 //     global scratch memory instead.  No block barriers.
 
-template <class K, int AMP, int KIND, int V>
+// on-chip bytes of one merge warp: a hash table of SW slots, or a sort
+// workspace of SW elements
+template <class K, int AMP, int ANN> __host__ __device__ constexpr size_t merge_warp_bytes(unsigned SW) {
+    return ANN == FQ_ANN_SORT_ARM ? SortWs<K, AMP>::bytes(SW) : (size_t)SW * slot_bytes<K, AMP>();
+}
+
+template <class K, int AMP, int KIND, int V, int ANN>
 __global__ void __launch_bounds__(Var<V>::WPB * 32, Var<V>::MINB)
 k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, unsigned G,
         unsigned SW, unsigned char* __restrict__ scratch, unsigned SS) {
@@ -859,8 +1031,13 @@ k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned gw = blockIdx.x * WPB + wib;
-    unsigned char* base_s = smem + (size_t)wib * SW * slot_bytes<K, AMP>();
-    unsigned char* base_g = scratch + (size_t)gw * SS * slot_bytes<K, AMP>();
+    unsigned char* base_s = smem + (size_t)wib * merge_warp_bytes<K, AMP, ANN>(SW);
+    // global scratch of the warp: a hash table of SS slots (hash arm), or a
+    // sort workspace of SS elements (sort arm), for buckets beyond the
+    // on-chip one
+    unsigned char* base_g =
+        scratch + (size_t)gw * (ANN == FQ_ANN_SORT_ARM ? SortWs<K, AMP>::bytes(SS)
+                                                       : (size_t)SS * slot_bytes<K, AMP>());
     K* const sk_s = (K*)base_s;
     ACC* const sa_s = (ACC*)(base_s + (size_t)SW * sizeof(K));
     unsigned* const sl_s = (unsigned*)(base_s + (size_t)SW * (sizeof(K) + sizeof(ACC)));
@@ -869,9 +1046,11 @@ k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     unsigned* const sl_g = (unsigned*)(base_g + (size_t)SS * (sizeof(K) + sizeof(ACC)));
     const K EMPTY = KeyOps<K>::empty();
 
-    for (unsigned q = lane; q < SW; q += 32) {
-        sk_s[q] = EMPTY;
-        sa_s[q] = (ACC)0;
+    if constexpr (ANN != FQ_ANN_SORT_ARM) {
+        for (unsigned q = lane; q < SW; q += 32) {
+            sk_s[q] = EMPTY;
+            sa_s[q] = (ACC)0;
+        }
     }
     __syncwarp();
     unsigned g0, g1;
@@ -950,6 +1129,20 @@ k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
                 a2_old = R->vcount[cur][seg + 2];
                 a2_sp = R->sfill[seg + 2];
             }
+        }
+        if constexpr (ANN == FQ_ANN_SORT_ARM) {
+            // the workspace holds the bucket's entries and spawns
+            const unsigned n = n_old + n_sp;
+            if (n <= SW) {
+                sort_bucket<K, AMP, KIND>(R, seg, cur, n_old, n_sp, base_s, SW, lane, acc);
+                ++acc.n_onchip;
+            } else if (n <= SS) {
+                sort_bucket<K, AMP, KIND>(R, seg, cur, n_old, n_sp, base_g, SS, lane, acc);
+                ++acc.n_scratch;
+            } else {
+                acc.full = true;
+            }
+            continue;
         }
         // the table holds the bucket's spawned addresses only
         const unsigned long long load = n_sp;
@@ -1245,7 +1438,7 @@ __global__ void k_seed(const RunDesc* __restrict__ R, const K* __restrict__ keys
     if (i >= n) return;
     const int cur = R->st->cur;
     const K key = keys[i];
-    const unsigned b = segment_of(seg_mix<K>(KeyOps<K>::rng_h(key)), R->log2B);
+    const unsigned b = segment_of(seg_hash(key), R->log2B);
     const unsigned pos = atomicAdd(&R->vcount[cur][b], 1u);
     if (pos < R->Cv) {
         ((K*)R->vkeys[cur])[(size_t)b * R->Cv + pos] = key;
@@ -1279,7 +1472,7 @@ __global__ void k_lookup(const RunDesc* __restrict__ R, const K* __restrict__ q,
     if (i >= n) return;
     const int cur = R->st->cur;
     const K key = q[i];
-    const unsigned b = segment_of(seg_mix<K>(KeyOps<K>::rng_h(key)), R->log2B);
+    const unsigned b = segment_of(seg_hash(key), R->log2B);
     const unsigned c = min(R->vcount[cur][b], R->Cv);
     const K* vk = (const K*)R->vkeys[cur] + (size_t)b * R->Cv;
     const A* va = (const A*)R->vamps[cur] + (size_t)b * R->Cv;
@@ -1337,7 +1530,7 @@ __global__ void k_ref_terms(ModelParams mp, const K* __restrict__ refs, const do
     tkeys[o] = key;
     th[o] = y[r] * MD::diagonal(mp, key);
     tv[o] = y[r];
-    tseg[o] = segment_of(seg_mix<K>(KeyOps<K>::rng_h(key)), log2B);
+    tseg[o] = segment_of(seg_hash(key), log2B);
     ++o;
     for (unsigned k = 0; k < m; ++k, ++o) {
         double hv;
@@ -1345,7 +1538,7 @@ __global__ void k_ref_terms(ModelParams mp, const K* __restrict__ refs, const do
         tkeys[o] = d;
         th[o] = y[r] * hv;
         tv[o] = 0.0;
-        tseg[o] = segment_of(seg_mix<K>(KeyOps<K>::rng_h(d)), log2B);
+        tseg[o] = segment_of(seg_hash(d), log2B);
     }
 }
 

@@ -29,9 +29,15 @@ template <class K, int AMP, int KIND> struct Launch {
     template <int V> static void merge_v(const LaunchCfg& c, const RunDesc* d, const unsigned* sr,
                                          unsigned G, cudaStream_t s) {
         constexpr int W = Var<V>::WPB;
-        const size_t smem = (size_t)W * c.slots * slot_bytes<K, AMP>();
-        k_merge<K, AMP, KIND, V><<<c.merge_grid, W * 32, smem, s>>>(d, sr, G, c.slots, c.scratch,
-                                                                    c.scratch_slots);
+        if (c.ann == FQ_ANN_SORT_ARM) {
+            const size_t smem = (size_t)W * merge_warp_bytes<K, AMP, FQ_ANN_SORT_ARM>(c.slots);
+            k_merge<K, AMP, KIND, V, FQ_ANN_SORT_ARM><<<c.merge_grid, W * 32, smem, s>>>(
+                d, sr, G, c.slots, c.sort_scratch, c.sort_elems);
+        } else {
+            const size_t smem = (size_t)W * merge_warp_bytes<K, AMP, FQ_ANN_HASH_ARM>(c.slots);
+            k_merge<K, AMP, KIND, V, FQ_ANN_HASH_ARM><<<c.merge_grid, W * 32, smem, s>>>(
+                d, sr, G, c.slots, c.scratch, c.scratch_slots);
+        }
     }
     static void merge(const LaunchCfg& c, const RunDesc* d, const unsigned* sr, unsigned G,
                       cudaStream_t s) {
@@ -40,8 +46,11 @@ template <class K, int AMP, int KIND> struct Launch {
         else merge_v<0>(c, d, sr, G, s);
     }
     template <int V> static cudaError_t prepare_v(size_t smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_merge<K, AMP, KIND, V>,
+        cudaError_t e = cudaFuncSetAttribute(k_merge<K, AMP, KIND, V, FQ_ANN_HASH_ARM>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_merge<K, AMP, KIND, V, FQ_ANN_SORT_ARM>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_spawn<K, AMP, KIND, V, 4>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -64,15 +73,24 @@ template <class K, int AMP, int KIND> struct Launch {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spawn<K, AMP, KIND, 0, 4>, 256, spawn_smem(8));
         return n;
     }
-    static int merge_occupancy(int var, size_t smem) {
+    template <int ANN> static int merge_occupancy_a(int var, size_t smem) {
         int n = 0;
         if (var == 1)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_merge<K, AMP, KIND, 1>, 128, smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_merge<K, AMP, KIND, 1, ANN>, 128, smem);
         else if (var == 2)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_merge<K, AMP, KIND, 2>, 128, smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_merge<K, AMP, KIND, 2, ANN>, 128, smem);
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_merge<K, AMP, KIND, 0>, 256, smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_merge<K, AMP, KIND, 0, ANN>, 256, smem);
         return n;
+    }
+    static int merge_occupancy(int ann, int var, size_t smem) {
+        return ann == FQ_ANN_SORT_ARM ? merge_occupancy_a<FQ_ANN_SORT_ARM>(var, smem)
+                                      : merge_occupancy_a<FQ_ANN_HASH_ARM>(var, smem);
+    }
+    static size_t merge_smem(int ann, int wpb, unsigned slots) {
+        return (size_t)wpb * (ann == FQ_ANN_SORT_ARM
+                                  ? merge_warp_bytes<K, AMP, FQ_ANN_SORT_ARM>(slots)
+                                  : merge_warp_bytes<K, AMP, FQ_ANN_HASH_ARM>(slots));
     }
     static void scratch_init(unsigned char* scratch, unsigned slots, unsigned nwarps,
                              cudaStream_t s) {
@@ -140,6 +158,8 @@ template <class K, int AMP, int KIND> struct Launch {
         k.spawn_occupancy = spawn_occupancy;
         k.scratch_init = scratch_init;
         k.merge_occupancy = merge_occupancy;
+        k.merge_smem = merge_smem;
+        k.sort_ws_bytes = SortWs<K, AMP>::bytes;
         k.seed = seed;
         k.gather_vec = gather_vec;
         k.gather_spawns = gather_spawns;

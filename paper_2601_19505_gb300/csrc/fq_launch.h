@@ -15,7 +15,9 @@ struct KernelSet {
     void (*merge)(const LaunchCfg&, const RunDesc*, const unsigned*, unsigned, cudaStream_t);
     cudaError_t (*prepare)(size_t merge_smem);
     int (*spawn_occupancy)(int var);               // resident blocks per SM
-    int (*merge_occupancy)(int var, size_t smem);
+    int (*merge_occupancy)(int ann, int var, size_t smem);
+    size_t (*merge_smem)(int ann, int wpb, unsigned slots);  // dynamic shared memory of a launch
+    size_t (*sort_ws_bytes)(unsigned elems);                 // one sort workspace
     void (*scratch_init)(unsigned char* scratch, unsigned slots, unsigned nwarps, cudaStream_t);
     void (*seed)(const RunDesc*, const void*, const double*, size_t, cudaStream_t);
     void (*gather_vec)(const void* keys, const void* amps, unsigned cap, const unsigned* cnt,

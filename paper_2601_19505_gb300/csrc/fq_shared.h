@@ -23,6 +23,10 @@
 #define FQ_DERR_TIMEOUT 16u
 #define FQ_DERR_RANGE 32u  // an amplitude beyond the exact-norm range
 
+// annihilation arms of the merge kernel
+#define FQ_ANN_HASH_ARM 0
+#define FQ_ANN_SORT_ARM 1
+
 #define FQ_MAX_MOM_MODES 64
 #define FQ_HIST_CAP 65536u
 
@@ -131,15 +135,19 @@ struct OverlapDesc {
 };
 
 struct LaunchCfg {
+    int ann;              // annihilation arm of the merge kernel (FQ_ANN_*_ARM)
     int spawn_var;        // compiled variant of the spawn kernel (warps, register cap)
     int spawn_wpb;        // its warps per block
     int spawn_grid;       // persistent spawn blocks
     int merge_var;        // compiled variant of the merge kernel
     int merge_wpb;        // its warps per block
     int merge_grid;       // persistent merge blocks
-    unsigned slots;       // on-chip table slots per merge warp (power of 2)
+    unsigned slots;       // per merge warp: on-chip hash-table slots (power of 2), or
+                          // sort-workspace elements
     unsigned scratch_slots;       // global scratch table slots per merge warp
     unsigned char* scratch;       // scratch tables, merge_grid * merge_wpb of them
+    unsigned sort_elems;          // global sort workspace elements per merge warp
+    unsigned char* sort_scratch;  // sort workspaces, merge_grid * merge_wpb of them
 };
 
 }  // namespace fq

@@ -363,10 +363,19 @@ class Run:
 
     def shape(self) -> dict:
         """The launch shape the run steps with (fq_run_shape)."""
-        v = (C.c_int * 6)()
+        v = (C.c_int * 7)()
         _check(self._lib.fq_run_shape(self.r, v), "fq_run_shape")
-        keys = ("spawn_wpb", "spawn_grid", "merge_wpb", "merge_grid", "slots", "scratch_slots")
-        return dict(zip(keys, [int(x) for x in v]))
+        keys = ("spawn_wpb", "spawn_grid", "merge_wpb", "merge_grid", "slots", "scratch_slots",
+                "annihilation")
+        out = dict(zip(keys, [int(x) for x in v]))
+        out["annihilation"] = {ANN_HASH: "hash", ANN_SORT: "sort"}.get(out["annihilation"], "?")
+        return out
+
+    def arm_times(self):
+        """fq_run_arm_times: the autotuner's best merge ms per arm, {"hash": ..., "sort": ...}."""
+        a, b = C.c_float(), C.c_float()
+        _check(self._lib.fq_run_arm_times(self.r, C.byref(a), C.byref(b)), "fq_run_arm_times")
+        return {"hash": a.value, "sort": b.value}
 
     def profile(self, n: int):
         """Mean ms per step of (spawn, merge, shift) over n eagerly launched steps."""
