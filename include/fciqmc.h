@@ -310,6 +310,19 @@ int fq_batch_autotune(fq_batch *b, int steps);
  * order, so repeated runs give identical rows.  Replaces any earlier
  * setting; FQ_ERR_INVALID for runs of different shapes or sizes. */
 int fq_batch_set_overlaps(fq_batch *b, const int *g2_d, int n_g2);
+/* Excited states (Sec. 2.2): runs 0..K-1 of the batch (2 <= K <= 8; one
+ * Hamiltonian and equal sizes; real-valued or deterministic walkers) become
+ * step-synchronised spectral states.  After every step's annihilation, run k
+ * is orthogonalised to runs 0..k-1 (Gram-Schmidt): c_k <- c_k - sum_j
+ * alpha_j c_j with alpha_j = (c_j^T c_k) / (c_j^T c_j), all alpha_j from the
+ * same c_k; each value that changed is then compressed by Pi (Eq.
+ * vec-compression, its draw from stream 0xFFFFFFFC of the address), and run
+ * k's norm, shift update and projected energy follow the orthogonalised
+ * vector.  The shift of run k estimates the k-th energy (shift_estimator).
+ * Seed the runs differently (a later state must not start parallel to an
+ * earlier one).  K = 0 turns it off; FQ_ERR_INVALID for integer walkers or
+ * runs of different shapes or sizes. */
+int fq_batch_set_spectral(fq_batch *b, int K);
 /* Move out the overlap rows recorded since the last call, oldest first, at
  * most cap of them (*n = rows written).  A row is `width` doubles: the step,
  * then per pair c_A^T c_B followed by its n_g2 G2 products; width =

@@ -115,6 +115,7 @@ def lib():
         L.or_shift_update.restype = C.c_double
         L.or_shift_update.argtypes = [C.c_double] * 7
         L.or_overlap.argtypes = [vp, vp, C.c_void_p, C.c_int, dp]
+        L.or_spectral_step.argtypes = [C.c_void_p, C.c_int, C.c_long]
         L.or_g2_diag.restype = C.c_double
         L.or_g2_diag.argtypes = [vp, kp, C.c_int]
         L.or_build_sparse.restype = C.c_long
@@ -342,6 +343,16 @@ def overlap(a: Run, b: Run, g2_d=()) -> np.ndarray:
     if lib().or_overlap(a.h, b.h, _ptr(d), len(d), out.ctypes.data_as(C.POINTER(C.c_double))):
         raise ValueError("G2 needs 1D real space and 0 <= d < M")
     return out
+
+
+def spectral_step(runs, n: int = 1) -> int:
+    """n steps of runs of one model, each run after the first orthogonalised to
+    the ones before it (Gram-Schmidt, Sec. 2.2); 0, or -5 if a population died."""
+    arr = (C.c_void_p * len(runs))(*[r.h for r in runs])
+    rc = lib().or_spectral_step(arr, len(runs), n)
+    if rc == -1:
+        raise ValueError("Gram-Schmidt needs 1 to 8 runs of real-valued walkers")
+    return rc
 
 
 def start_run(model: Model, params: Params, weight: float = 10.0, shift=None) -> Run:

@@ -806,7 +806,10 @@ void or_run_record_spawns(void *p, int on) { ((or_run *)p)->record = on; }
  * (Eq. shift-update).  Contributions to an address are summed diagonal term
  * first, then spawns by (source address, attempt).  Returns -5 when the
  * population dies (norm 0). */
-static int one_step(or_run *r) {
+typedef struct { int64_t n_exact, n_inexact, n_spawns; } step_counts;
+
+/* The new vector of one step (spawning, annihilation, compression). */
+static void step_vector(or_run *r, step_counts *sc) {
     uint32_t step = (uint32_t)(r->step + 1);
     clist cl = {0};
     int64_t n_exact = 0, n_inexact = 0, n_spawns = 0;
@@ -854,7 +857,13 @@ static int one_step(or_run *r) {
     free(cl.c);
     free(r->vec);
     r->vec = nv; r->n = nn; r->cap = cl.n;
+    sc->n_exact = n_exact; sc->n_inexact = n_inexact; sc->n_spawns = n_spawns;
+}
 
+/* The end of a step: the norm of the new vector, the shift update and the
+ * history row.  Returns -5 when the population died. */
+static int step_finish(or_run *r, const step_counts *sc) {
+    uint32_t step = (uint32_t)(r->step + 1);
     double norm = exact_norm(r);
     r->step = step;
     if (norm == 0.0) { r->norm = 0.0; return -5; }
@@ -864,7 +873,7 @@ static int one_step(or_run *r) {
 
     or_stats st;
     st.step = r->step; st.len = r->n;
-    st.exact_steps = n_exact; st.inexact_steps = n_inexact; st.n_spawns = n_spawns;
+    st.exact_steps = sc->n_exact; st.inexact_steps = sc->n_inexact; st.n_spawns = sc->n_spawns;
     st.shift = r->shift; st.norm = norm;
     projections(r, &st.hproj, &st.vproj);
     if (r->n_hist == r->cap_hist) {
@@ -873,6 +882,12 @@ static int one_step(or_run *r) {
     }
     r->hist[r->n_hist++] = st;
     return 0;
+}
+
+static int one_step(or_run *r) {
+    step_counts sc;
+    step_vector(r, &sc);
+    return step_finish(r, &sc);
 }
 
 int or_run_step(void *p, long nsteps) {
@@ -1004,6 +1019,114 @@ double or_g2_diag(const void *pm, const okey *k, int d) {
     uint8_t occ[OR_MAXM];
     decode_key(md, *k, occ);
     return g2_diag(md, occ, d);
+}
+
+/* ------------------------------------------------------------------------ */
+/* excited states (Sec. 2.2): K step-synchronised runs, the k-th
+ * orthogonalised to the ones before it after every step (Gram-Schmidt)      */
+
+static double dot_sorted(const or_run *a, const or_run *b) {
+    double s = 0.0;
+    long i = 0, j = 0;
+    while (i < a->n && j < b->n) {
+        int c = key_cmp(a->vec[i].key, b->vec[j].key);
+        if (c < 0) { ++i; continue; }
+        if (c > 0) { ++j; continue; }
+        s += a->vec[i].amp * b->vec[j].amp;
+        ++i; ++j;
+    }
+    return s;
+}
+
+/* c_k <- c_k - sum_{j<k} alpha_j c_j with alpha_j = (c_j^T c_k) / (c_j^T c_j)
+ * (classical Gram-Schmidt: every alpha_j from the same c_k, the c_j already
+ * orthogonalised this step).  Readings (the paper names the method only):
+ * (i) the dot products are FP64 sums in ascending address order; (ii) per
+ * address the terms are subtracted in order j = 0, 1, ..., each as
+ * v - alpha_j c_j (FP32 arithmetic with FP32 alpha for REAL32 runs); (iii) a
+ * value that changed is then compressed by Pi (Eq. vec-compression, the
+ * draw of stream 0xFFFFFFFC of its address and run), so the vector stays
+ * as sparse as a step leaves it; the deterministic limit compresses
+ * nothing.  Integer walkers are not supported (returns -1). */
+static int orthogonalise(or_run **runs, int k) {
+    or_run *rk = runs[k];
+    if (rk->pr.mode == OR_INT) return -1;
+    double alpha[8];
+    for (int j = 0; j < k; ++j) {
+        double djj = dot_sorted(runs[j], runs[j]);
+        alpha[j] = djj != 0.0 ? dot_sorted(runs[j], rk) / djj : 0.0;
+    }
+    long cap = rk->n;
+    for (int j = 0; j < k; ++j) cap += runs[j]->n;
+    entry *nv = (entry *)malloc(sizeof(entry) * (size_t)(cap > 0 ? cap : 1));
+    long *pos = (long *)calloc((size_t)(k + 1), sizeof(long));
+    long nn = 0;
+    uint32_t step = (uint32_t)(rk->step + 1);
+    const int f32 = rk->pr.mode == OR_REAL32;
+    for (;;) {
+        /* the smallest address not yet taken from any of the k + 1 lists */
+        int have = 0;
+        okey a = {0, 0};
+        for (int j = 0; j <= k; ++j) {
+            const or_run *rj = j < k ? runs[j] : rk;
+            if (pos[j] < rj->n && (!have || key_cmp(rj->vec[pos[j]].key, a) < 0)) {
+                a = rj->vec[pos[j]].key;
+                have = 1;
+            }
+        }
+        if (!have) break;
+        double v = 0.0;
+        if (pos[k] < rk->n && key_cmp(rk->vec[pos[k]].key, a) == 0) v = rk->vec[pos[k]++].amp;
+        int changed = 0;
+        for (int j = 0; j < k; ++j) {
+            const or_run *rj = runs[j];
+            if (pos[j] < rj->n && key_cmp(rj->vec[pos[j]].key, a) == 0) {
+                double cj = rj->vec[pos[j]++].amp;
+                if (f32) v = (double)((float)v - (float)alpha[j] * (float)cj);
+                else v = v - alpha[j] * cj;
+                changed = 1;
+            }
+        }
+        double out = v;
+        if (changed && rk->pr.mode != OR_DETERMINISTIC) {
+            if (v == 0.0) continue;
+            if (fabs(v) < rk->pr.threshold) {
+                uint32_t w[4];
+                draw(&rk->pr, step, 0xFFFFFFFCu, rng_h(&rk->md, a), w);
+                if (!(uniform53(w) < fabs(v) / rk->pr.threshold)) continue;
+                out = store_round(rk->pr.mode, copysign(rk->pr.threshold, v));
+            }
+        }
+        if (out == 0.0) continue;
+        nv[nn].key = a;
+        nv[nn].amp = out;
+        nn++;
+    }
+    free(pos);
+    free(rk->vec);
+    rk->vec = nv; rk->n = nn; rk->cap = cap;
+    return 0;
+}
+
+/* nsteps steps of K runs (one model, K <= 8): every run's new vector, then
+ * runs 1..K-1 orthogonalised in order, then each run's norm, shift update
+ * and history row.  Returns -1 for integer walkers, -5 when a population
+ * died. */
+int or_spectral_step(void **pruns, int K, long nsteps) {
+    or_run *runs[8];
+    if (K < 1 || K > 8) return -1;
+    for (int k = 0; k < K; ++k) runs[k] = (or_run *)pruns[k];
+    for (long n = 0; n < nsteps; ++n) {
+        step_counts sc[8];
+        for (int k = 0; k < K; ++k) step_vector(runs[k], &sc[k]);
+        for (int k = 1; k < K; ++k)
+            if (orthogonalise(runs, k)) return -1;
+        for (int k = 0; k < K; ++k) {
+            int rc = step_finish(runs[k], &sc[k]);
+            if (rc) return rc;
+        }
+    }
+    return 0;
 }
 
 /* ------------------------------------------------------------------------ */

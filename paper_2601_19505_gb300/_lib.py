@@ -83,6 +83,7 @@ SYMBOLS = {
     "fq_run_profile": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_float)]),
     "fq_run_arm_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "fq_batch_set_overlaps": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "fq_batch_set_spectral": (C.c_int, [C.c_void_p, C.c_int]),
     "fq_batch_overlaps": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t),
                                     C.POINTER(C.c_int)]),
     "fq_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int]),

@@ -155,6 +155,14 @@ struct fq_batch {
     unsigned ov_cap, ov_table;
     int ov_grid, ov_wpb;
     unsigned long long ov_read;  // rows handed out so far
+    // excited states (fq_batch_set_spectral)
+    int gs_K;
+    GsDesc* d_gs;
+    double* gs_part;
+    double* gs_alpha;
+    size_t gs_part_n;
+    unsigned gs_table;
+    int gs_grid, gs_wpb;
 };
 
 // ---------------------------------------------------------------------------
@@ -1011,11 +1019,18 @@ static void launch_overlaps(fq_batch* b, cudaStream_t s) {
     if (b->ov_on) b->ks->overlap(b->d_desc, b->d_ov, b->ov_grid, b->ov_wpb, b->ov_table, s);
 }
 
+// Gram-Schmidt of the spectral states, between the merge and the shift update
+static void launch_gs(fq_batch* b, cudaStream_t s) {
+    for (int k = 1; k < b->gs_K; ++k)
+        b->ks->gs(b->d_desc, b->d_gs, k, b->gs_grid, b->gs_wpb, b->gs_table, s);
+}
+
 static void enqueue_steps(fq_batch* b, int n, cudaStream_t s) {
     const int nr = (int)b->runs.size();
     for (int i = 0; i < n; ++i) {
         b->ks->spawn(b->cfg, b->d_desc, b->d_seg_run, b->G, s);
         b->ks->merge(b->cfg, b->d_desc, b->d_seg_run, b->G, s);
+        launch_gs(b, s);
         launch_shift(b->d_desc, nr, s);
         launch_overlaps(b, s);
     }
@@ -1093,10 +1108,58 @@ static int overlaps_build(fq_batch* b) {
     return FQ_OK;
 }
 
+static void gs_free(fq_batch* b) {
+    if (b->d_gs) cudaFree(b->d_gs);
+    if (b->gs_part) cudaFree(b->gs_part);
+    if (b->gs_alpha) cudaFree(b->gs_alpha);
+    b->d_gs = nullptr;
+    b->gs_part = b->gs_alpha = nullptr;
+    b->gs_part_n = 0;
+    b->gs_K = 0;
+}
+
+// the Gram-Schmidt launches for the batch's current sizes: one table per
+// warp with at least twice the slots of K segments' entries
+static int gs_build(fq_batch* b) {
+    if (b->gs_K < 2) return FQ_OK;
+    unsigned cv = 0;
+    for (int k = 0; k < b->gs_K; ++k) cv = std::max(cv, b->runs[k]->Cv);
+    const unsigned T = std::max(64u, next_pow2(2ull * b->gs_K * cv));
+    const size_t slot = b->ks->gs_slot_bytes;
+    if ((size_t)T * slot > 200u * 1024u) return FQ_ERR_INVALID;  // segments too large
+    int wpb = 4;
+    while (wpb > 1 && (size_t)wpb * T * slot > 200u * 1024u) wpb >>= 1;
+    CK(b->ks->prepare_gs((size_t)wpb * T * slot));
+    const unsigned B = b->runs[0]->B;
+    b->gs_wpb = wpb;
+    b->gs_grid = (int)std::max<unsigned long long>(
+        1, std::min<unsigned long long>((unsigned long long)num_sms() * (8 / wpb),
+                                        ((unsigned long long)B + wpb - 1) / wpb));
+    b->gs_table = T;
+    const size_t need = (size_t)b->gs_grid * wpb * 2 * FQ_MAX_SPECTRAL;
+    if (need > b->gs_part_n) {
+        if (b->gs_part) cudaFree(b->gs_part);
+        b->gs_part = nullptr;
+        b->gs_part_n = 0;
+        CK(cudaMalloc((void**)&b->gs_part, sizeof(double) * need));
+        b->gs_part_n = need;
+    }
+    GsDesc g;
+    memset(&g, 0, sizeof g);
+    g.K = b->gs_K;
+    g.B = B;
+    g.table = T;
+    g.part = b->gs_part;
+    g.alpha = b->gs_alpha;
+    CK(cudaMemcpy(b->d_gs, &g, sizeof g, cudaMemcpyHostToDevice));
+    return FQ_OK;
+}
+
 static void batch_free(fq_batch* b) {
     if (!b) return;
     batch_release(b);
     overlaps_free(b);
+    gs_free(b);
     fq_run* r0 = b->runs[0];
     if (b->scratch) {
         if (r0->has_alloc) r0->alloc.free(r0->alloc.ctx, b->scratch, b->scratch_bytes, (void*)r0->stream);
@@ -1227,7 +1290,8 @@ static int batch_build(fq_batch* b) {
         c.sort_elems = se;
     }
     {
-        const int rc = overlaps_build(b);
+        int rc = overlaps_build(b);
+        if (!rc) rc = gs_build(b);
         if (rc) return rc;
     }
     b->cfg = b->shapes[0];
@@ -1675,6 +1739,7 @@ static int autotune(fq_batch* b, int steps) {
         cudaEventRecord(ev[3 * t + 1], b->stream);
         b->ks->merge(c, b->d_desc, b->d_seg_run, b->G, b->stream);
         e = cudaEventRecord(ev[3 * t + 2], b->stream);
+        launch_gs(b, b->stream);
         launch_shift(b->d_desc, nr, b->stream);
         launch_overlaps(b, b->stream);
     }
@@ -1853,6 +1918,36 @@ extern "C" int fq_batch_set_overlaps(fq_batch* b, const int* g2_d, int n_g2) {
     batch_release(b);
     int rc = batch_build(b);
     if (rc) overlaps_free(b);
+    return rc;
+}
+
+extern "C" int fq_batch_set_spectral(fq_batch* b, int K) {
+    if (!b || K < 0 || K > FQ_MAX_SPECTRAL || K > (int)b->runs.size()) return FQ_ERR_INVALID;
+    if (K >= 2) {
+        const fq_run* r0 = b->runs[0];
+        for (int k = 0; k < K; ++k) {
+            const fq_run* r = b->runs[k];
+            if (r->B != r0->B || r->amp == FQ_AMP_INT || r->ham.mp.M != r0->ham.mp.M ||
+                r->ham.mp.N != r0->ham.mp.N || r->ham.mp.kind != r0->ham.mp.kind ||
+                r->ham.mp.Lx != r0->ham.mp.Lx)
+                return FQ_ERR_INVALID;
+        }
+    }
+    CK(cudaStreamSynchronize(b->stream));
+    gs_free(b);
+    if (K >= 2) {
+        CK(cudaMalloc((void**)&b->d_gs, sizeof(GsDesc)));
+        CK(cudaMalloc((void**)&b->gs_alpha, sizeof(double) * FQ_MAX_SPECTRAL));
+        b->gs_K = K;
+    }
+    batch_release(b);
+    int rc = batch_build(b);
+    if (rc) {
+        gs_free(b);
+        batch_release(b);
+        const int rc2 = batch_build(b);
+        (void)rc2;
+    }
     return rc;
 }
 

@@ -620,18 +620,15 @@ __device__ __forceinline__ bool is_taken(long long x) {
 
 // Pi, compaction and the norm terms of one merged value, for a warp of lanes
 // (keep: the lane has a value)
+// compaction and the norm terms of the values a warp keeps (keep: the lane
+// stores `out` at `key`)
 template <class K, int AMP>
-__device__ __forceinline__ void merge_emit(const RunDesc* R, bool has, K key,
-                                           typename AmpT<AMP>::ACC w, uint2 rkey, unsigned stepno,
-                                           K* __restrict__ ok, typename AmpT<AMP>::A* __restrict__ oa,
-                                           unsigned Cv, int nq, int det, int early, int lane,
-                                           unsigned& nout, MergeAcc& acc) {
-    typedef typename AmpT<AMP>::ACC ACC;
+__device__ __forceinline__ void merge_store(const RunDesc* R, bool keep, K key,
+                                            typename AmpT<AMP>::ACC out, K* __restrict__ ok,
+                                            typename AmpT<AMP>::A* __restrict__ oa, unsigned Cv,
+                                            int nq, int det, int lane, unsigned& nout,
+                                            MergeAcc& acc) {
     typedef typename AmpT<AMP>::A A;
-    ACC out = (ACC)0;
-    // early compression stores the sums as they are (Eq. early-comp)
-    const bool keep = has && (early ? ((out = w) != (ACC)0)
-                                    : compress<AMP>(w, R, rkey, stepno, KeyOps<K>::rng_h(key), out));
     const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
     if (keep) {
         const unsigned pos = nout + (unsigned)__popc(bal & ((1u << lane) - 1u));
@@ -658,6 +655,20 @@ __device__ __forceinline__ void merge_emit(const RunDesc* R, bool has, K key,
         }
     }
     nout += (unsigned)__popc(bal);
+}
+
+template <class K, int AMP>
+__device__ __forceinline__ void merge_emit(const RunDesc* R, bool has, K key,
+                                           typename AmpT<AMP>::ACC w, uint2 rkey, unsigned stepno,
+                                           K* __restrict__ ok, typename AmpT<AMP>::A* __restrict__ oa,
+                                           unsigned Cv, int nq, int det, int early, int lane,
+                                           unsigned& nout, MergeAcc& acc) {
+    typedef typename AmpT<AMP>::ACC ACC;
+    ACC out = (ACC)0;
+    // early compression stores the sums as they are (Eq. early-comp)
+    const bool keep = has && (early ? ((out = w) != (ACC)0)
+                                    : compress<AMP>(w, R, rkey, stepno, KeyOps<K>::rng_h(key), out));
+    merge_store<K, AMP>(R, keep, key, out, ok, oa, Cv, nq, det, lane, nout, acc);
 }
 
 // The end of a bucket: the projected-energy terms whose address falls in it
@@ -1413,6 +1424,209 @@ static __global__ void k_overlap_row(const RunDesc* __restrict__ runs,
     if (threadIdx.x == 0) row[0] = (double)runs[0].st->step;
     __syncthreads();
     if (threadIdx.x == 0) *od->head = h + 1;
+}
+
+// ---------------------------------------------------------------------------
+// excited states (Sec. 2.2): Gram-Schmidt on the step's new vectors (in
+// buffer cur ^ 1 until k_shift flips it).  For the run k being
+// orthogonalised: k_gs_dots sums c_j^T c_k and c_j^T c_j for j < k per warp,
+// k_gs_alpha adds the partials in warp order and forms alpha_j =
+// (c_j^T c_k) / (c_j^T c_j), and k_gs_axpy forms c_k - sum_j alpha_j c_j
+// segment by segment in an on-chip table (subtracting j = 0, 1, ... in turn),
+// compresses every changed value by Pi with the draw of stream 0xFFFFFFFC of
+// its address, and rewrites run k's segment in place with its norm terms.
+
+template <class K, int AMP>
+__global__ void __launch_bounds__(128) k_gs_dots(const RunDesc* __restrict__ runs,
+                                                 const GsDesc* __restrict__ gs, int k) {
+    typedef typename AmpT<AMP>::A A;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const unsigned T = gs->table;
+    unsigned char* base = smem + (size_t)wib * T * (sizeof(K) + sizeof(double) + sizeof(unsigned));
+    K* const tk = (K*)base;
+    double* const ta = (double*)(base + (size_t)T * sizeof(K));
+    unsigned* const tl = (unsigned*)(base + (size_t)T * (sizeof(K) + sizeof(double)));
+    const K EMPTY = KeyOps<K>::empty();
+    for (unsigned q = lane; q < T; q += 32) tk[q] = EMPTY;
+    __syncwarp();
+    const unsigned gw = blockIdx.x * wpb + wib, nw = gridDim.x * wpb;
+    double acc[2 * FQ_MAX_SPECTRAL];
+    for (int i = 0; i < 2 * k; ++i) acc[i] = 0.0;
+    const RunDesc* Rk = runs + k;
+    const int ck = Rk->st->cur ^ 1;
+    unsigned g0, g1;
+    warp_range(gs->B, gw, nw, g0, g1);
+    for (unsigned seg = g0; seg < g1; ++seg) {
+        const unsigned nk = min(Rk->vcount[ck][seg], Rk->Cv);
+        const K* kk = (const K*)Rk->vkeys[ck] + (size_t)seg * Rk->Cv;
+        const A* ka = (const A*)Rk->vamps[ck] + (size_t)seg * Rk->Cv;
+        unsigned nl = 0;
+        for (unsigned i0 = 0; i0 < nk; i0 += 32) {
+            const unsigned i = i0 + lane;
+            bool is_new = false;
+            int q = -1;
+            if (i < nk) {
+                q = table_insert(tk, T - 1u, kk[i], is_new);
+                if (q >= 0) ta[q] = (double)ka[i];
+            }
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, is_new);
+            if (is_new) tl[nl + __popc(bal & ((1u << lane) - 1u))] = (unsigned)q;
+            nl += __popc(bal);
+        }
+        __syncwarp();
+        for (int j = 0; j < k; ++j) {
+            const RunDesc* Rj = runs + j;
+            const int cj = Rj->st->cur ^ 1;
+            const unsigned nj = min(Rj->vcount[cj][seg], Rj->Cv);
+            const K* jk = (const K*)Rj->vkeys[cj] + (size_t)seg * Rj->Cv;
+            const A* ja = (const A*)Rj->vamps[cj] + (size_t)seg * Rj->Cv;
+            for (unsigned i = lane; i < nj; i += 32) {
+                const double v = (double)ja[i];
+                acc[2 * j + 1] += v * v;
+                if (nk) {
+                    const int q = table_find(tk, T - 1u, jk[i]);
+                    if (q >= 0) acc[2 * j] += v * ta[q];
+                }
+            }
+        }
+        __syncwarp();
+        for (unsigned i = lane; i < nl; i += 32) tk[tl[i]] = EMPTY;
+        __syncwarp();
+    }
+    double* part = gs->part + (size_t)gw * 2 * FQ_MAX_SPECTRAL;
+    for (int i = 0; i < 2 * k; ++i) {
+        const double v = warp_sum(acc[i]);
+        if (lane == 0) part[i] = v;
+    }
+}
+
+// the coefficients alpha_j of run k from the per-warp partial sums (warp
+// order); run k's norm accumulators restart for k_gs_axpy
+static __global__ void k_gs_alpha(const RunDesc* __restrict__ runs, const GsDesc* __restrict__ gs,
+                                  int k, unsigned nwarps) {
+    __shared__ double d[2 * FQ_MAX_SPECTRAL];
+    const int t = threadIdx.x;
+    if (t < 2 * k) {
+        double s = 0.0;
+        for (unsigned w = 0; w < nwarps; ++w) s += gs->part[(size_t)w * 2 * FQ_MAX_SPECTRAL + t];
+        d[t] = s;
+    }
+    __syncthreads();
+    if (t == 0) {
+        for (int j = 0; j < k; ++j) gs->alpha[j] = d[2 * j + 1] != 0.0 ? d[2 * j] / d[2 * j + 1] : 0.0;
+        RunState* st = runs[k].st;
+        st->norm_lo = 0;
+        st->norm_hi = 0;
+        st->norm_fp = 0.0;
+        st->len_acc = 0;
+    }
+}
+
+template <class K, int AMP, int KIND>
+__global__ void __launch_bounds__(128) k_gs_axpy(const RunDesc* __restrict__ runs,
+                                                 const GsDesc* __restrict__ gs, int k) {
+    typedef typename AmpT<AMP>::A A;
+    typedef typename AmpT<AMP>::ACC ACC;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const unsigned T = gs->table;
+    unsigned char* base =
+        smem + (size_t)wib * T * (sizeof(K) + sizeof(ACC) + sizeof(unsigned) + 1);
+    K* const tk = (K*)base;
+    ACC* const ta = (ACC*)(base + (size_t)T * sizeof(K));
+    unsigned* const tl = (unsigned*)(base + (size_t)T * (sizeof(K) + sizeof(ACC)));
+    unsigned char* const tc = base + (size_t)T * (sizeof(K) + sizeof(ACC) + sizeof(unsigned));
+    const K EMPTY = KeyOps<K>::empty();
+    for (unsigned q = lane; q < T; q += 32) {
+        tk[q] = EMPTY;
+        tc[q] = 0;
+    }
+    __syncwarp();
+    const unsigned gw = blockIdx.x * wpb + wib, nw = gridDim.x * wpb;
+    const RunDesc* R = runs + k;
+    unsigned e = 0;
+    if (lane == 0)
+        for (int j = 0; j <= k; ++j) e |= *(volatile unsigned*)&runs[j].st->err;
+    if (__shfl_sync(0xFFFFFFFFu, e, 0)) return;  // the step fails and is rolled back
+    const int cur = R->st->cur, ck = cur ^ 1;
+    const unsigned Cv = R->Cv;
+    const unsigned stepno = (unsigned)(R->st->step + 1);
+    const uint2 rkey = make_uint2(R->key_x, R->key_y);
+    const int nq = R->norm_q, det = R->mode_det;
+    double alpha[FQ_MAX_SPECTRAL];
+    for (int j = 0; j < k; ++j) alpha[j] = gs->alpha[j];
+    MergeAcc acc = {0, 0, 0, 0.0, false, false, false, 0, 0, 0};
+    unsigned g0, g1;
+    warp_range(gs->B, gw, nw, g0, g1);
+    for (unsigned seg = g0; seg < g1; ++seg) {
+        const unsigned nk = min(R->vcount[ck][seg], Cv);
+        K* const kk = (K*)R->vkeys[ck] + (size_t)seg * Cv;
+        A* const ka = (A*)R->vamps[ck] + (size_t)seg * Cv;
+        unsigned nl = 0;
+        // run k's entries, then each earlier run's contribution in turn
+        for (int j = -1; j < k; ++j) {
+            const RunDesc* Rj = j < 0 ? R : runs + j;
+            const int cj = j < 0 ? ck : (Rj->st->cur ^ 1);
+            const unsigned nj = j < 0 ? nk : min(Rj->vcount[cj][seg], Rj->Cv);
+            const K* jk = (const K*)Rj->vkeys[cj] + (size_t)seg * Rj->Cv;
+            const A* ja = (const A*)Rj->vamps[cj] + (size_t)seg * Rj->Cv;
+            for (unsigned i0 = 0; i0 < nj; i0 += 32) {
+                const unsigned i = i0 + lane;
+                bool is_new = false;
+                int q = -1;
+                if (i < nj) {
+                    q = table_insert(tk, T - 1u, jk[i], is_new);
+                    if (q < 0) {
+                        acc.full = true;
+                    } else if (j < 0) {
+                        ta[q] = (ACC)ja[i];
+                    } else {
+                        const ACC v = is_new ? (ACC)0 : ta[q];
+                        if constexpr (AMP == FQ_AMP_F32)
+                            ta[q] = v - (float)alpha[j] * ja[i];
+                        else
+                            ta[q] = v - (ACC)(alpha[j] * (double)ja[i]);
+                        tc[q] = 1;
+                    }
+                }
+                const unsigned bal = __ballot_sync(0xFFFFFFFFu, is_new);
+                if (is_new) tl[nl + __popc(bal & ((1u << lane) - 1u))] = (unsigned)q;
+                nl += __popc(bal);
+            }
+            __syncwarp();
+        }
+        // changed values compressed (Pi, stream 0xFFFFFFFC), then compacted
+        // back into run k's segment
+        unsigned nout = 0;
+        for (unsigned b0 = 0; b0 < nl; b0 += 32) {
+            const unsigned i = b0 + lane;
+            bool keep = false;
+            ACC w = (ACC)0;
+            K key = EMPTY;
+            if (i < nl) {
+                const unsigned q = tl[i];
+                key = tk[q];
+                w = ta[q];
+                keep = w != (ACC)0;
+                if constexpr (AMP != FQ_AMP_INT) {  // integer walkers never get here
+                    if (keep && tc[q] && !det && !at_least_theta(w, R)) {
+                        const uint4 r4 = draw(rkey, stepno, 0xFFFFFFFCu, KeyOps<K>::rng_h(key));
+                        keep = pi_below(w, r4, R);
+                    }
+                }
+            }
+            merge_store<K, AMP>(R, keep, key, w, kk, ka, Cv, nq, det, lane, nout, acc);
+        }
+        __syncwarp();
+        bucket_finish<K, AMP>(R, seg, cur, nout, kk, ka, lane);
+        for (unsigned i = lane; i < nl; i += 32) {
+            tk[tl[i]] = EMPTY;
+            tc[tl[i]] = 0;
+        }
+        __syncwarp();
+    }
+    merge_flush(R, acc, lane);
 }
 
 // ---------------------------------------------------------------------------

@@ -146,6 +146,22 @@ template <class K, int AMP, int KIND> struct Launch {
         return cudaFuncSetAttribute(k_overlap<K, AMP, KIND>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
+    static constexpr size_t gs_dots_slot() { return sizeof(K) + sizeof(double) + sizeof(unsigned); }
+    static constexpr size_t gs_axpy_slot() { return sizeof(K) + sizeof(ACC) + sizeof(unsigned) + 1; }
+    static void gs(const RunDesc* d, const GsDesc* g, int k, int grid, int wpb, unsigned table,
+                   cudaStream_t s) {
+        k_gs_dots<K, AMP><<<grid, wpb * 32, (size_t)wpb * table * gs_dots_slot(), s>>>(d, g, k);
+        k_gs_alpha<<<1, 32, 0, s>>>(d, g, k, (unsigned)(grid * wpb));
+        k_gs_axpy<K, AMP, KIND><<<grid, wpb * 32, (size_t)wpb * table * gs_axpy_slot(), s>>>(d, g, k);
+    }
+    static cudaError_t prepare_gs(size_t smem) {
+        cudaError_t e = cudaFuncSetAttribute(k_gs_dots<K, AMP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_gs_axpy<K, AMP, KIND>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return e;
+    }
     static KernelSet make() {
         KernelSet k;
         k.key_bytes = sizeof(K);
@@ -170,6 +186,9 @@ template <class K, int AMP, int KIND> struct Launch {
         k.ref_terms = ref_terms;
         k.overlap = overlap;
         k.prepare_overlap = prepare_overlap;
+        k.gs = gs;
+        k.prepare_gs = prepare_gs;
+        k.gs_slot_bytes = gs_dots_slot() > gs_axpy_slot() ? gs_dots_slot() : gs_axpy_slot();
         k.overlap_slot_bytes = sizeof(K) + sizeof(double) + sizeof(unsigned);
         return k;
     }

@@ -39,6 +39,11 @@ struct KernelSet {
                     unsigned table, cudaStream_t);
     size_t overlap_slot_bytes;  // one slot of an overlap table: key, FP64 amplitude, list entry
     cudaError_t (*prepare_overlap)(size_t smem);
+    // Gram-Schmidt of run k: dot products, coefficients, axpy (grid x wpb warps)
+    void (*gs)(const RunDesc* runs, const GsDesc* gs, int k, int grid, int wpb, unsigned table,
+               cudaStream_t);
+    cudaError_t (*prepare_gs)(size_t smem);
+    size_t gs_slot_bytes;  // one slot of the axpy table: key, value, list entry, flag
 };
 
 // kw = 64-bit words per address (1 or 2), amp = FQ_AMP_*, kind = FQ_KIND_*

@@ -134,6 +134,18 @@ struct OverlapDesc {
     unsigned cap;                  // rows the ring holds
 };
 
+// Excited states (Sec. 2.2): runs 0..K-1 of a batch are step-synchronised
+// spectral states; after every step's merge, run k >= 1 is orthogonalised to
+// runs 0..k-1 (Gram-Schmidt) on the new vectors, segment by segment.
+#define FQ_MAX_SPECTRAL 8
+struct GsDesc {
+    int K;                  // spectral states
+    unsigned B;             // segments per run
+    unsigned table;         // slots of a warp's table (power of 2)
+    double* part;           // per warp: 2 FQ_MAX_SPECTRAL partial dot products
+    double* alpha;          // FQ_MAX_SPECTRAL coefficients of the run being orthogonalised
+};
+
 struct LaunchCfg {
     int ann;              // annihilation arm of the merge kernel (FQ_ANN_*_ARM)
     int spawn_var;        // compiled variant of the spawn kernel (warps, register cap)

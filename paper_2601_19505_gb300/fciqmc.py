@@ -421,6 +421,10 @@ class Batch:
         d = np.ascontiguousarray(g2_d, dtype=np.int32)
         _check(self._lib.fq_batch_set_overlaps(self.b, _ptr(d), len(d)), "fq_batch_set_overlaps")
 
+    def set_spectral(self, K: int):
+        """fq_batch_set_spectral: runs 0..K-1 as spectral states, orthogonalised every step."""
+        _check(self._lib.fq_batch_set_spectral(self.b, int(K)), "fq_batch_set_spectral")
+
     def overlaps(self, cap: int = 1 << 16) -> np.ndarray:
         """fq_batch_overlaps: the rows recorded since the last call, shape (rows, width)."""
         w = C.c_int()

@@ -178,3 +178,55 @@ def test_early_compression_terms_and_no_compression_limit():
     k, v = e.export()
     assert np.any(np.abs(v) < 1.0)
     assert O.exact_norm(v, 1.0, O.MODE_REAL64) == e.state()[1]
+
+
+def _spectral_pair(m, mode, seed, target):
+    s = m.start()
+    nb = m.column(s)[0][0]
+    a = O.Run(m, O.default_params(mode=mode, dt=0.01, target=target, seed=seed))
+    a.seed([s], [10.0], m.diagonal(s), 0)
+    b = O.Run(m, O.default_params(mode=mode, dt=0.01, target=target, seed=seed, run_id=1))
+    b.seed([s, nb], [10.0, 10.0], m.diagonal(s), 0)
+    return a, b
+
+
+def test_gram_schmidt_deterministic_limit_gives_the_first_excited_state():
+    """Excited states (Sec. 2.2): in the deterministic limit the first run is
+    the power iteration of Eq. fciqmc and the second, orthogonalised to it
+    after every step, converges to the next eigenvector; the shifts then equal
+    the two lowest eigenvalues of exact diagonalisation."""
+    m = O.Model(O.REAL_1D, 6, 1, 6, 1.0, 6.0)
+    e = ED.lowest(m, 2)
+    a, b = _spectral_pair(m, O.MODE_DETERMINISTIC, 1, 1e3)
+    assert O.spectral_step([a, b], 8000) == 0
+    assert abs(a.state()[0] - e[0]) < 1e-8
+    assert abs(b.state()[0] - e[1]) < 1e-6
+    # the two vectors are orthogonal after the last step
+    (ka, va), (kb, vb) = a.export(), b.export()
+    da = {O.key_int(k): x for k, x in zip(ka, va)}
+    dot = sum(da.get(O.key_int(k), 0.0) * x for k, x in zip(kb, vb))
+    assert abs(dot) < 1e-12 * np.linalg.norm(va) * np.linalg.norm(vb)
+    with pytest.raises(Exception):
+        ai, bi = _spectral_pair(m, O.MODE_INT, 1, 1e3)
+        assert O.spectral_step([ai, bi], 1) == 0
+
+
+def test_gram_schmidt_stochastic_excited_energy_within_two_sigma():
+    """Two compressed FP64 runs (N_t = 1e4, seeds 1..3): the blocked shift of
+    the orthogonalised run, pooled over the seeds, lies within 2 sigma of the
+    first excited energy, and the first run's within 2 sigma of the ground
+    energy."""
+    m = O.Model(O.REAL_1D, 6, 1, 6, 1.0, 6.0)
+    e = ED.lowest(m, 2)
+    est = [[], []]
+    for seed in (1, 2, 3):
+        a, b = _spectral_pair(m, O.MODE_REAL64, seed, 1e4)
+        assert O.spectral_step([a, b], 6000) == 0
+        for i, r in enumerate((a, b)):
+            s = BL.blocking_analysis(list(r.history()["shift"][1000:]))
+            est[i].append((s["mean"], s["err"]))
+    for i in range(2):
+        w = np.array([1.0 / x[1] ** 2 for x in est[i]])
+        mean = float(np.dot([x[0] for x in est[i]], w) / w.sum())
+        err = float(1.0 / np.sqrt(w.sum()))
+        assert abs(mean - e[i]) < 2 * err, (i, mean, err, e[i])
