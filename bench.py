@@ -328,7 +328,8 @@ def gpu_arm(args, cfg, name, dist, with_cpu=True):
     rank, world, local = dist_env()
     h = fq.Hamiltonian(cfg["kind"], cfg["Lx"], cfg["Ly"], cfg["N"], cfg["t"], cfg["u"])
     p = fq.default_params(mode=MODE_CODE[cfg["mode"]], dt=cfg["dt"], target=cfg["target"],
-                          seed=cfg["seed"], run_id=rank, annihilation=ANN_CODE[args.annihilation])
+                          seed=cfg["seed"], run_id=rank, annihilation=ANN_CODE[args.annihilation],
+                          capacity_vec=int(args.capacity_vec), capacity_spawn=int(args.capacity_spawn))
     run = fq.Run(h, p)
     run.seed_default(W.START_WEIGHT)
     equil = args.equil if args.equil is not None else cfg["steps"] // 4
@@ -656,7 +657,7 @@ def c3_trajectory_arm(args):
         done = 0
         while done < steps:
             k = min(250, steps - done)
-            run.advance(k, chunk=k)
+            run.advance(k, chunk=50, grow=2.0, max_grows=40)
             rows.append(run.history())
             done += k
         hist = np.concatenate(rows)
@@ -694,6 +695,10 @@ def main():
     ap.add_argument("--equil", type=int, default=None)
     ap.add_argument("--target", type=float, default=None,
                     help="override the workload's N_t (reduced cases for profiling)")
+    ap.add_argument("--capacity-vec", type=float, default=0,
+                    help="vector capacity in entries (0: derived from N_t)")
+    ap.add_argument("--capacity-spawn", type=float, default=0,
+                    help="spawn capacity per step in entries (0: derived from N_t)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--annihilation", choices=sorted(ANN_CODE), default="auto",
                     help="annihilation arm (auto: the autotuner times hash and sort)")
@@ -721,9 +726,10 @@ def main():
         cfg["mode"] = "REAL64"  # the paper's arithmetic; c5 as configured is nested below
     elif args.mode:
         cfg["mode"] = args.mode
+    if args.target or args.capacity_vec or args.capacity_spawn:
+        headline = False
     if args.target:
         cfg["target"] = args.target
-        headline = False
     if args.impl == "reference":
         return reference_arm(args, cfg, args.config)
     import torch

@@ -16,7 +16,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libfciqmc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "--fmad=false", "-lineinfo", "-Xcompiler", "-fPIC",
+FLAGS = ["-O3", "-std=c++17", "--fmad=false", "-lineinfo", "-Werror", "cross-execution-space-call",
+         "-Xcompiler", "-fPIC",
          "-Xcompiler", "-ffp-contract=off", "-I", CSRC, "-I", INCLUDE]
 
 

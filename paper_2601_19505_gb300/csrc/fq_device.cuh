@@ -287,59 +287,25 @@ template <int KIND> struct RealModel {
             else val = __ldg(p.hop_tab + ns * (nt + 1));
             return dest;
         }
-        // 2D: the neighbouring site s2 from the model's table.  Every
-        // direction takes one path (no divergence within a warp): the
-        // target run's start q is found by counting separators from P inside
-        // one 64-bit window of the address, and only the bits between the
-        // two runs change -- moving a boson from site s to a later site
-        // shifts bits [P, q) down by one and sets bit q - 1; to an earlier
-        // site it shifts bits [q, P] up by one and sets bit q.  Targets
-        // beyond the window take the search from bit 0.
+        // 2D: the neighbouring site from the model's table; a hop to the
+        // next or previous site moves one separator (as in 1D), any other
+        // removes a one-bit at P and inserts one at the start of the target
+        // run, located from P by counting separators in a 64-bit window
         typedef KeyOps<K> O;
         const int s = P - O::popc(key & O::low(P));
+        const int ns = run_from(key, P);
         const int s2 = p.nbr[d][s];
-        const uint64_t wu = window_up(key, P);  // bit i = bit P + i
-        int ns = -1, nt = -1;
-        K dest = key;
-        if (~wu) {
-            ns = __ffsll((long long)~wu) - 1;
-            if (s2 > s) {
-                const uint64_t z = ~wu;
-                const int j = s2 - s;
-                const int L = __popcll(z) >= j ? nth_set64(z, j - 1) + 1 : 64;  // q - P
-                if (L < 64) {
-                    const uint64_t up = wu >> L;             // bit i = bit q + i
-                    const int r2 = __ffsll((long long)~up) - 1;
-                    if (L + r2 < 64) {                       // the target run ends inside
-                        nt = r2;
-                        const uint64_t w = wu & ((1ull << L) - 1ull);
-                        const uint64_t nw = (w >> 1) | (1ull << (L - 1));
-                        dest = key ^ O::shl((K)(w ^ nw), P);
-                    }
-                }
-            } else if (s2 > 0) {
-                const uint64_t wd = window_down(key, P);  // bit 63 = bit P - 1
-                const uint64_t z = __brevll(~wd);         // bit t = zero at P - 1 - t
-                const int j = s - s2 + 1;
-                if (__popcll(z) >= j) {
-                    const int t = nth_set64(z, j - 1);    // t >= 1: q = P - t
-                    const uint64_t below = wd >> (64 - t);  // bits q .. P - 1
-                    nt = __ffsll((long long)~below) - 1;
-                    const uint64_t w = below | (1ull << t);  // bits q .. P
-                    const uint64_t nw = ((w << 1) | 1ull) & (t == 63 ? ~0ull : ((2ull << t) - 1ull));
-                    dest = key ^ O::shl((K)(w ^ nw), P - t);
-                }
-            } else if (P < 63) {  // to site 0: q = 0, bits 0 .. P
-                const uint64_t below = window_down(key, P) >> (64 - P);  // bits 0 .. P - 1 (P >= 1)
-                nt = __ffsll((long long)~below) - 1;
-                const uint64_t w = below | (1ull << P);
-                const uint64_t nw = ((w << 1) | 1ull) & ((2ull << P) - 1ull);
-                dest = key ^ (K)(w ^ nw);
-            }
-        }
-        if (nt < 0) {  // the search from bit 0
-            ns = run_from(key, P);
-            const int q = mode_start(key, s2);
+        int nt;
+        K dest;
+        if (s2 == s + 1) {
+            nt = run_from(key, P + ns + 1);
+            dest = key ^ ((K)3 << (P + ns - 1));
+        } else if (s2 == s - 1) {
+            const K z = ~key & O::low(P - 1);
+            nt = z ? (P - 2 - (O::W - 1 - clz_k(z))) : (P - 1);
+            dest = key ^ ((K)3 << (P - 1));
+        } else {
+            const int q = mode_start_from(key, P, s, s2);
             nt = run_from(key, q);
             dest = ins_one(del_bit(key, P), q - (s2 > s ? 1 : 0));
         }

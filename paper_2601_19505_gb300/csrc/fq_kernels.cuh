@@ -402,9 +402,13 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
                 wm[i] = mm;
             }
             const unsigned x = cnt > 1u ? cnt - 1u : 0u;
-            const unsigned incl = warp_incl_scan(x, lane);
-            woff[i] = xoff + incl - x;
-            xoff += __shfl_sync(0xFFFFFFFFu, incl, 31);
+            if (__any_sync(0xFFFFFFFFu, x)) {
+                const unsigned incl = warp_incl_scan(x, lane);
+                woff[i] = xoff + incl - x;
+                xoff += __shfl_sync(0xFFFFFFFFu, incl, 31);
+            } else {  // no further attempts in this round (one pick per source)
+                woff[i] = xoff;
+            }
             K dest = KeyOps<K>::empty();
             S val = (S)0;
             const bool has = cnt >= 1u && make_col(key, col, cf, mm, 0u, dest, val);
@@ -892,7 +896,7 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
 // 16-bit index arrays, then 256 digit counters
 template <class K, int AMP> struct SortWs {
     typedef typename AmpT<AMP>::ACC ACC;
-    static constexpr size_t al(size_t b) { return (b + 15) / 16 * 16; }
+    __host__ __device__ static constexpr size_t al(size_t b) { return (b + 15) / 16 * 16; }
     __host__ __device__ static constexpr size_t val_off(unsigned C) { return al((size_t)C * sizeof(K)); }
     __host__ __device__ static constexpr size_t hash_off(unsigned C) {
         return val_off(C) + al((size_t)C * sizeof(ACC));

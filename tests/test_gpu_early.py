@@ -24,7 +24,7 @@ def test_early_compression_spawns_and_steps(model, mode):
     rtol = 1e-12 if mode == "REAL64" else 1e-5
     keys, amps = seeded_vector(m, 3000, 5, mode=mode)
     g, o = runs(h, m, mode=mcode, dt=0.003, target=1e5, seed=42, run_id=3, compression=EARLY,
-                capacity_vec=20000, capacity_spawn=400000)
+                capacity_vec=400000, capacity_spawn=800000)
     g.seed(fq().keys_from_ints(keys), amps, -1.5, step=17)
     o.seed(keys, amps, -1.5, step=17)
     o.record_spawns()
