@@ -655,9 +655,15 @@ def c3_trajectory_arm(args):
         rows = []
         t0 = time.perf_counter()
         done = 0
+        stopped = None
         while done < steps:
-            k = min(250, steps - done)
-            run.advance(k, chunk=50, grow=2.0, max_grows=40)
+            k = min(50, steps - done)
+            try:
+                run.advance(k, chunk=50, grow=2.0, max_grows=12)
+            except fq.FqError as e:  # the population outgrew the device memory
+                stopped = "%s (capacity %s)" % (e, list(run.capacity()))
+                rows.append(run.history())
+                break
             rows.append(run.history())
             done += k
         hist = np.concatenate(rows)
@@ -666,10 +672,12 @@ def c3_trajectory_arm(args):
         release_device_memory()
         half = hist[len(hist) // 2:]
         rec = {"mode": mode, "target": target, "steps": int(len(hist)), "wall_s": wall,
+               "stopped": stopped,
                "norm_over_target_last_half": float(np.mean(half["norm"]) / target),
                "len_max": int(hist["len"].max()), "step_of_len_max": int(hist["step"][np.argmax(hist["len"])]),
-               "trajectory_every_50": [[int(r["step"]), int(r["len"]), float(r["norm"]),
-                                        float(r["shift"])] for r in hist[::50]]}
+               "trajectory_every_10": [[int(r["step"]), int(r["len"]), float(r["norm"]),
+                                        float(r["shift"]), int(r["n_spawns"]),
+                                        int(r["exact_steps"])] for r in hist[::10]]}
         sh = A.blocked_mean(half["shift"])
         e = A.ratio_estimate(half["hproj"], half["vproj"])
         rec["shift_last_half"] = [sh["mean"], sh["err"]]
@@ -677,7 +685,7 @@ def c3_trajectory_arm(args):
         out["runs"].append(rec)
         return rec
 
-    for target in (1e6, 1e7):
+    for target in (1e5, 1e6):
         for mode in ("REAL32", "REAL64"):
             one(mode, target, cfg["steps"])
     one("REAL32", cfg["target"], args.steps)

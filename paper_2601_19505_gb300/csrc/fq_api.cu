@@ -706,8 +706,8 @@ extern "C" int fq_run_create(fq_run** out, const fq_ham* h, const fq_params* p, 
         r->vkeys[i] = A(kb * (size_t)B * r->Cv);
         r->vamps[i] = A(ab * (size_t)B * r->Cv);
     }
-    r->skeys = A(kb * (size_t)B * r->Cs);
-    r->samps = A(sb * (size_t)B * r->Cs);
+    r->skeys = A(r->ks->spawn_key_stride * (size_t)B * r->Cs);
+    r->samps = A(std::max<size_t>(16, r->ks->spawn_val_stride * (size_t)B * r->Cs));
     r->sfill = (unsigned*)A(sizeof(unsigned) * B);
     r->part_h = (double*)A(sizeof(double) * B);
     r->part_v = (double*)A(sizeof(double) * B);
@@ -1524,8 +1524,8 @@ extern "C" int fq_run_reserve(fq_run* r, size_t capacity_vec, size_t capacity_sp
         r->Cv = Cv;
     }
     if (Cs > r->Cs) {
-        void* nk = dev_alloc(r, kb * (size_t)r->B * Cs);
-        void* nv = dev_alloc(r, sb * (size_t)r->B * Cs);
+        void* nk = dev_alloc(r, r->ks->spawn_key_stride * (size_t)r->B * Cs);
+        void* nv = dev_alloc(r, std::max<size_t>(16, r->ks->spawn_val_stride * (size_t)r->B * Cs));
         if (!nk || !nv) {
             if (nk) dev_free(r, nk);
             if (nv) dev_free(r, nv);

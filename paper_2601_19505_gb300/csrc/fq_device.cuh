@@ -127,40 +127,6 @@ template <class K> __device__ __forceinline__ K add_boson(K k, int s) {
 // bits that start a run of ones: one per occupied mode
 template <class K> __device__ __forceinline__ K run_starts(K k) { return k & ~(k << 1); }
 
-// bits [p, p + 64) of x (0 above the top), and bits [p - 64, p) with bit
-// p - 1 at the top (0 below bit 0); 0 <= p <= W
-__device__ __forceinline__ uint64_t window_up(uint64_t x, int p) { return p >= 64 ? 0ull : x >> p; }
-__device__ __forceinline__ uint64_t window_up(u128 x, int p) {
-    return p >= 128 ? 0ull : (uint64_t)(x >> p);
-}
-__device__ __forceinline__ uint64_t window_down(uint64_t x, int p) {
-    return p <= 0 ? 0ull : x << (64 - p);
-}
-__device__ __forceinline__ uint64_t window_down(u128 x, int p) {
-    return p <= 0 ? 0ull : (uint64_t)((x << (128 - p)) >> 64);
-}
-
-// start bit of mode s2 of address k, given the start P of an occupied mode
-// s != s2.  Counting separators from P: for s2 > s, separator s2 - 1 is the
-// (s2 - s)-th zero at or above P; for s2 < s, it is the (s - s2 + 1)-th zero
-// below P.  Found in one 64-bit window around P when it holds that many
-// zeros (always, unless over 50-odd bosons sit between the two modes), else
-// by the search from bit 0.  Zeros past either end of the address are never
-// reached first: the separator sought lies inside it.
-template <class K> __device__ __forceinline__ int mode_start_from(K k, int P, int s, int s2) {
-    if (s2 > s) {
-        const uint64_t z = ~window_up(k, P);
-        const int j = s2 - s;
-        if (__popcll(z) >= j) return P + nth_set64(z, j - 1) + 1;
-    } else {
-        if (s2 == 0) return 0;
-        const uint64_t z = __brevll(~window_down(k, P));  // bit t = bit P - 1 - t
-        const int j = s - s2 + 1;
-        if (__popcll(z) >= j) return P - nth_set64(z, j - 1);
-    }
-    return mode_start(k, s2);
-}
-
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and the draw layout:
 //   key     = (seed_lo32, seed_hi32 ^ run_id * 0x9E3779B9)
@@ -290,7 +256,8 @@ template <int KIND> struct RealModel {
         // 2D: the neighbouring site from the model's table; a hop to the
         // next or previous site moves one separator (as in 1D), any other
         // removes a one-bit at P and inserts one at the start of the target
-        // run, located from P by counting separators in a 64-bit window
+        // run, located once (a search from P within a 64-bit window measured
+        // slower than this search from bit 0)
         typedef KeyOps<K> O;
         const int s = P - O::popc(key & O::low(P));
         const int ns = run_from(key, P);
@@ -305,7 +272,7 @@ template <int KIND> struct RealModel {
             nt = z ? (P - 2 - (O::W - 1 - clz_k(z))) : (P - 1);
             dest = key ^ ((K)3 << (P - 1));
         } else {
-            const int q = mode_start_from(key, P, s, s2);
+            const int q = mode_start(key, s2);
             nt = run_from(key, q);
             dest = ins_one(del_bit(key, P), q - (s2 > s ? 1 : 0));
         }

@@ -59,6 +59,49 @@ template <> struct Var<2> { static constexpr int WPB = 4, MINB = 6; };
 constexpr int kVariants = 3;
 
 // ---------------------------------------------------------------------------
+// Spawn buffers.  64-bit addresses: a key array and a value array.  128-bit
+// addresses: one 32-byte record per spawn (address, value, zero padding),
+// which fills exactly one 32-byte DRAM sector, so a spawn is stored as a
+// whole sector and the memory system never has to read the sector's old
+// contents to merge a partial write (spawns land in random buckets, so the
+// sectors of separate 16-byte keys and 8-byte values were mostly written
+// partly).  `kb` and `vb` are the run's skeys and samps; entry i of bucket b
+// is at i = b Cs + position.
+template <class K, class S> struct SpawnIO {
+    static constexpr bool REC = sizeof(K) == 16;
+    static constexpr size_t key_bytes = REC ? 32 : sizeof(K);  // bytes per entry of kb
+    static constexpr size_t val_bytes = REC ? 0 : sizeof(S);   // bytes per entry of vb
+    __device__ __forceinline__ static void store(void* kb, void* vb, size_t i, K key, S v) {
+        if constexpr (REC) {
+            uint4* p = (uint4*)((unsigned char*)kb + i * 32);
+            const unsigned long long lo = (unsigned long long)key;
+            const unsigned long long hi = (unsigned long long)(key >> 32 >> 32);
+            p[0] = make_uint4((unsigned)lo, (unsigned)(lo >> 32), (unsigned)hi, (unsigned)(hi >> 32));
+            unsigned long long vbits = 0;
+            memcpy(&vbits, &v, sizeof(S));
+            p[1] = make_uint4((unsigned)vbits, (unsigned)(vbits >> 32), 0u, 0u);
+        } else {
+            ((K*)kb)[i] = key;
+            ((S*)vb)[i] = v;
+        }
+    }
+    __device__ __forceinline__ static void load(const void* kb, const void* vb, size_t i, K& key,
+                                                S& v) {
+        if constexpr (REC) {
+            const uint4* p = (const uint4*)((const unsigned char*)kb + i * 32);
+            const uint4 a = p[0], b = p[1];
+            key = (K)(((unsigned long long)a.y << 32) | a.x) |
+                  ((K)(((unsigned long long)a.w << 32) | a.z) << 32 << 32);
+            const unsigned long long vbits = ((unsigned long long)b.y << 32) | b.x;
+            memcpy(&v, &vbits, sizeof(S));
+        } else {
+            key = ((const K*)kb)[i];
+            v = ((const S*)vb)[i];
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
 // warp-level helpers
 
 __device__ __forceinline__ unsigned warp_incl_scan(unsigned x, int lane) {
@@ -168,8 +211,8 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     const A* va0 = nullptr;
     const unsigned* vcnt = nullptr;
     unsigned Cv = 0, Cs = 0, stepno = 0;
-    K* sk = nullptr;
-    S* sv = nullptr;
+    void* sk = nullptr;
+    void* sv = nullptr;
     unsigned* sfill = nullptr;
     int log2B = 0;
     double dt = 0.0;
@@ -186,8 +229,7 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     auto flush_pending = [&]() {
         if (!ph) return;
         if (pp < Cs) {
-            sk[(size_t)pb * Cs + pp] = pd;
-            sv[(size_t)pb * Cs + pp] = pv;
+            SpawnIO<K, S>::store(sk, sv, (size_t)pb * Cs + pp, pd, pv);
         } else {
             atomicOr(&R->st->err, FQ_DERR_SPAWN_CAP);
         }
@@ -226,8 +268,8 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
         vcnt = R->vcount[cur];
         Cv = R->Cv;
         Cs = R->Cs;
-        sk = (K*)R->skeys;
-        sv = (S*)R->samps;
+        sk = R->skeys;
+        sv = R->samps;
         sfill = R->sfill;
         log2B = R->log2B;
         dt = R->st->dt;
@@ -775,8 +817,9 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
     const A* __restrict__ va = (const A*)R->vamps[cur] + (size_t)seg * Cv;
     K* __restrict__ ok = (K*)R->vkeys[cur ^ 1] + (size_t)seg * Cv;
     A* __restrict__ oa = (A*)R->vamps[cur ^ 1] + (size_t)seg * Cv;
-    const K* __restrict__ sk = (const K*)R->skeys + (size_t)seg * R->Cs;
-    const S* __restrict__ sv = (const S*)R->samps + (size_t)seg * R->Cs;
+    const void* const skb = R->skeys;
+    const void* const svb = R->samps;
+    const size_t s0 = (size_t)seg * R->Cs;
     const unsigned stepno = (unsigned)(R->st->step + 1);
     const uint2 rkey = make_uint2(R->key_x, R->key_y);
     const int nq = R->norm_q;
@@ -788,18 +831,16 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
     // before the current ones are inserted.
     unsigned nl = 0;
     {
-        K skey = lane < n_sp ? sk[lane] : EMPTY;
-        S sval = lane < n_sp ? sv[lane] : (S)0;
+        K skey = EMPTY;
+        S sval = (S)0;
+        if (lane < n_sp) SpawnIO<K, S>::load(skb, svb, s0 + lane, skey, sval);
         for (unsigned j0 = 0; j0 < n_sp; j0 += 32) {
             const unsigned j = j0 + lane;
             bool nw = false;
             int q = -1;
             const K key = skey;
             const S v = sval;
-            if (j + 32 < n_sp) {
-                skey = sk[j + 32];
-                sval = sv[j + 32];
-            }
+            if (j + 32 < n_sp) SpawnIO<K, S>::load(skb, svb, s0 + j + 32, skey, sval);
             if (j < n_sp) {
                 q = table_insert(tk, mask, key, nw);
                 if (q < 0) acc.full = true;
@@ -925,8 +966,7 @@ __device__ __forceinline__ void sort_bucket(const RunDesc* R, unsigned seg, unsi
     const A* __restrict__ va = (const A*)R->vamps[cur] + (size_t)seg * Cv;
     K* __restrict__ ok = (K*)R->vkeys[cur ^ 1] + (size_t)seg * Cv;
     A* __restrict__ oa = (A*)R->vamps[cur ^ 1] + (size_t)seg * Cv;
-    const K* __restrict__ sk = (const K*)R->skeys + (size_t)seg * R->Cs;
-    const S* __restrict__ sv = (const S*)R->samps + (size_t)seg * R->Cs;
+    const size_t s0 = (size_t)seg * R->Cs;
     const unsigned stepno = (unsigned)(R->st->step + 1);
     const uint2 rkey = make_uint2(R->key_x, R->key_y);
     const int nq = R->norm_q, det = R->mode_det, early = R->early;
@@ -946,10 +986,12 @@ __device__ __forceinline__ void sort_bucket(const RunDesc* R, unsigned seg, unsi
         ia[i] = (unsigned short)i;
     }
     for (unsigned j = lane; j < n_sp; j += 32) {
-        const K key = sk[j];
+        K key;
+        S sval;
+        SpawnIO<K, S>::load(R->skeys, R->samps, s0 + j, key, sval);
         const unsigned i = n_old + j;
         wk[i] = key;
-        wv[i] = (ACC)sv[j];
+        wv[i] = (ACC)sval;
         wh[i] = hash16(key);
         ia[i] = (unsigned short)i;
     }
@@ -1131,10 +1173,12 @@ k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
                             Cv * (unsigned)sizeof(K));
                 prefetch_l2((const A*)R->vamps[cur] + vo, po * (unsigned)sizeof(A),
                             Cv * (unsigned)sizeof(A));
-                prefetch_l2((const K*)R->skeys + so, ps * (unsigned)sizeof(K),
-                            Cs * (unsigned)sizeof(K));
-                prefetch_l2((const S*)R->samps + so, ps * (unsigned)sizeof(S),
-                            Cs * (unsigned)sizeof(S));
+                typedef SpawnIO<K, S> IO;
+                prefetch_l2((const unsigned char*)R->skeys + so * IO::key_bytes,
+                            ps * (unsigned)IO::key_bytes, Cs * (unsigned)IO::key_bytes);
+                if (IO::val_bytes)
+                    prefetch_l2((const unsigned char*)R->samps + so * IO::val_bytes,
+                                ps * (unsigned)IO::val_bytes, Cs * (unsigned)IO::val_bytes);
             }
             ahead_g = g + 1;
             a1_old = o1;
@@ -1715,6 +1759,24 @@ __global__ void k_gather(const K* __restrict__ keys, const T* __restrict__ vals,
         for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
             okeys[o + i] = keys[(size_t)b * cap + i];
             ovals[o + i] = (double)vals[(size_t)b * cap + i];
+        }
+    }
+}
+
+// the same for spawn buckets, in their layout
+template <class K, class S>
+__global__ void k_gather_spawns(const void* __restrict__ kb, const void* __restrict__ vb,
+                                unsigned cap, const unsigned* __restrict__ cnt,
+                                const unsigned* __restrict__ off, unsigned B, K* __restrict__ okeys,
+                                double* __restrict__ ovals) {
+    for (unsigned b = blockIdx.x; b < B; b += gridDim.x) {
+        const unsigned n = min(cnt[b], cap), o = off[b];
+        for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+            K key;
+            S v;
+            SpawnIO<K, S>::load(kb, vb, (size_t)b * cap + i, key, v);
+            okeys[o + i] = key;
+            ovals[o + i] = (double)v;
         }
     }
 }

@@ -119,8 +119,8 @@ template <class K, int AMP, int KIND> struct Launch {
     static void gather_spawns(const void* keys, const void* vals, unsigned cap, const unsigned* cnt,
                               const unsigned* off, unsigned B, void* okeys, double* ovals,
                               cudaStream_t s) {
-        k_gather<K, S><<<B < 4096 ? B : 4096, 256, 0, s>>>((const K*)keys, (const S*)vals, cap, cnt,
-                                                           off, B, (K*)okeys, ovals, nullptr);
+        k_gather_spawns<K, S><<<B < 4096 ? B : 4096, 256, 0, s>>>(keys, vals, cap, cnt, off, B,
+                                                                  (K*)okeys, ovals);
     }
     static void column(const ModelParams& mp, const void* key, void* dest, double* val,
                        unsigned cap, double* diag, unsigned* m, cudaStream_t s) {
@@ -167,6 +167,8 @@ template <class K, int AMP, int KIND> struct Launch {
         k.key_bytes = sizeof(K);
         k.amp_bytes = sizeof(A);
         k.spawn_bytes = sizeof(S);
+        k.spawn_key_stride = SpawnIO<K, S>::key_bytes;
+        k.spawn_val_stride = SpawnIO<K, S>::val_bytes;
         k.slot_bytes = slot_bytes<K, AMP>();
         k.spawn = spawn;
         k.merge = merge;

@@ -10,6 +10,7 @@ namespace fq {
 
 struct KernelSet {
     size_t key_bytes, amp_bytes, spawn_bytes;
+    size_t spawn_key_stride, spawn_val_stride;  // spawn buffer bytes per entry (SpawnIO)
     size_t slot_bytes;  // one merge table slot: key, sum, list entry
     void (*spawn)(const LaunchCfg&, const RunDesc*, const unsigned*, unsigned, cudaStream_t);
     void (*merge)(const LaunchCfg&, const RunDesc*, const unsigned*, unsigned, cudaStream_t);

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from gpu_helpers import fq, pair
+from gpu_helpers import assert_same_vector, fq, pair
 
 pytestmark = pytest.mark.gpu
 
@@ -49,6 +49,11 @@ def test_overlap_rows_match_oracle(model, ds, mode, rtol):
         rows = b.overlaps()
         assert rows.shape == (10, width)
         assert np.array_equal(rows[:, 0], np.arange(10 * block + 1, 10 * block + 11))
+        # each replica follows the oracle's trajectory ...
+        for g, o in zip(runs, oruns):
+            assert_same_vector(g.export(), o.export(), rtol=rtol if mode else 0.0,
+                               what="replica run_id %d step %d" % (runs.index(g), 10 * block + 10))
+        # ... and the overlap row equals the oracle's overlaps of the same vectors
         want = np.concatenate([O.overlap(oruns[a], oruns[c], ds) for a, c in pairs])
         got = rows[-1, 1:]
         assert np.allclose(got, want, rtol=rtol, atol=0), (block, got, want)

