@@ -612,6 +612,8 @@ def c3_precision_arm(args):
             st = run.stats()
         run.reserve(int(5e8), int(1e9))  # the timed steps keep growing ~25 % each
         before = run.stats()
+        run.autotune(1)  # both annihilation arms timed on this vector
+        arms = run.arm_times()
         n = min(args.steps, 3)
         ms = run.profile(n)
         hist = run.history()
@@ -619,6 +621,7 @@ def c3_precision_arm(args):
         t = (ms[0] + ms[1] + ms[2]) * 1e-3 * n
         out[mode] = {"configs_per_s": units / t, "ms_per_step": 1e3 * t / n,
                      "kernel_ms": {"spawn": ms[0], "merge": ms[1], "shift": ms[2]},
+                     "autotuner_merge_ms_per_arm": arms, "annihilation": run.shape()["annihilation"],
                      "step": before["step"], "len": before["len"], "norm": before["norm"]}
         run.close()
         del run
@@ -647,9 +650,11 @@ def c3_trajectory_arm(args):
     cfg = dict(W.CONFIGS["c3"])
     out = {"workload": describe(cfg, "c3"), "runs": []}
 
-    def one(mode, target, steps):
+    def one(mode, target, steps, zeta=None):
         h = fq.Hamiltonian(cfg["kind"], cfg["Lx"], cfg["Ly"], cfg["N"], cfg["t"], cfg["u"])
-        p = fq.default_params(mode=MODE_CODE[mode], dt=cfg["dt"], target=target, seed=cfg["seed"])
+        kw = {} if zeta is None else {"zeta": zeta}
+        p = fq.default_params(mode=MODE_CODE[mode], dt=cfg["dt"], target=target, seed=cfg["seed"],
+                              **kw)
         run = fq.Run(h, p)
         run.seed_default(W.START_WEIGHT)
         rows = []
@@ -671,8 +676,8 @@ def c3_trajectory_arm(args):
         run.close()
         release_device_memory()
         half = hist[len(hist) // 2:]
-        rec = {"mode": mode, "target": target, "steps": int(len(hist)), "wall_s": wall,
-               "stopped": stopped,
+        rec = {"mode": mode, "target": target, "zeta": p.zeta, "xi": p.xi,
+               "steps": int(len(hist)), "wall_s": wall, "stopped": stopped,
                "norm_over_target_last_half": float(np.mean(half["norm"]) / target),
                "len_max": int(hist["len"].max()), "step_of_len_max": int(hist["step"][np.argmax(hist["len"])]),
                "trajectory_every_10": [[int(r["step"]), int(r["len"]), float(r["norm"]),
@@ -689,6 +694,10 @@ def c3_trajectory_arm(args):
         for mode in ("REAL32", "REAL64"):
             one(mode, target, cfg["steps"])
     one("REAL32", cfg["target"], args.steps)
+    # the damping scaled with the time step: zeta / dt = 8, as the defaults
+    # have at dt = 0.01 (and xi = zeta^2 / 4)
+    for mode in ("REAL32", "REAL64"):
+        one(mode, 1e6, cfg["steps"], zeta=0.08 * cfg["dt"] / 0.01)
     print(json.dumps({"metric": METRIC + " (c3 trajectories)", "c3_trajectory": out}), flush=True)
     return 0
 

@@ -65,8 +65,16 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
     return z ^ (z >> 31);
 }
 
+// 128-bit addresses.  Shifts by a variable amount are written out on the two
+// 64-bit halves, with the amounts 0, 64 and >= 128 taken explicitly: the
+// compiled unsigned __int128 shift by exactly 64 bits produced a wrong low
+// word (bit(64) came out as bits 0 and 64), which corrupted hops whose bit
+// position is 64.  Shifts by a constant stay on the 128-bit type.
 template <> struct KeyOps<u128> {
     static constexpr int W = 128;
+    __device__ __forceinline__ static u128 make(uint64_t lo, uint64_t hi) {
+        return ((u128)hi << 64) | (u128)lo;
+    }
     __device__ __forceinline__ static u128 empty() { return ~(u128)0; }
     __device__ __forceinline__ static int popc(u128 k) {
         return __popcll((uint64_t)k) + __popcll((uint64_t)(k >> 64));
@@ -76,16 +84,35 @@ template <> struct KeyOps<u128> {
         int c = __popcll(lo);
         return j < c ? nth_set64(lo, j) : 64 + nth_set64((uint64_t)(k >> 64), j - c);
     }
-    __device__ __forceinline__ static u128 shr(u128 x, int s) { return s >= 128 ? (u128)0 : x >> s; }
-    __device__ __forceinline__ static u128 shl(u128 x, int s) { return s >= 128 ? (u128)0 : x << s; }
-    __device__ __forceinline__ static u128 low(int p) { return p >= 128 ? ~(u128)0 : (((u128)1 << p) - 1); }
+    __device__ __forceinline__ static u128 shr(u128 x, int s) {
+        const uint64_t lo = (uint64_t)x, hi = (uint64_t)(x >> 64);
+        if (s <= 0) return x;
+        if (s >= 128) return (u128)0;
+        if (s >= 64) return make(s == 64 ? hi : hi >> (s - 64), 0ull);
+        return make((lo >> s) | (hi << (64 - s)), hi >> s);
+    }
+    __device__ __forceinline__ static u128 shl(u128 x, int s) {
+        const uint64_t lo = (uint64_t)x, hi = (uint64_t)(x >> 64);
+        if (s <= 0) return x;
+        if (s >= 128) return (u128)0;
+        if (s >= 64) return make(0ull, s == 64 ? lo : lo << (s - 64));
+        return make(lo << s, (hi << s) | (lo >> (64 - s)));
+    }
+    __device__ __forceinline__ static u128 low(int p) {
+        if (p <= 0) return (u128)0;
+        if (p >= 128) return ~(u128)0;
+        if (p >= 64) return make(~0ull, p == 64 ? 0ull : (1ull << (p - 64)) - 1ull);
+        return make((1ull << p) - 1ull, 0ull);
+    }
     __device__ __forceinline__ static int ctz(u128 x) {
         uint64_t lo = (uint64_t)x, hi = (uint64_t)(x >> 64);
         if (lo) return __ffsll((long long)lo) - 1;
         if (hi) return 64 + __ffsll((long long)hi) - 1;
         return 128;
     }
-    __device__ __forceinline__ static u128 bit(int p) { return (u128)1 << p; }
+    __device__ __forceinline__ static u128 bit(int p) {
+        return p >= 64 ? make(0ull, 1ull << (p - 64)) : make(1ull << p, 0ull);
+    }
     __device__ __forceinline__ static uint64_t rng_h(u128 k) {
         return (uint64_t)k ^ splitmix64((uint64_t)(k >> 64));
     }
@@ -233,20 +260,20 @@ template <int KIND> struct RealModel {
             if (d == 0) {
                 if (P + ns == nb) {  // last mode -> mode 0
                     nt = run_from(key, 0);
-                    dest = ((key & ~O::bit(nb - 1)) << 1) | (K)1;
+                    dest = O::shl(key & ~O::bit(nb - 1), 1) | (K)1;
                 } else {
                     nt = run_from(key, P + ns + 1);
-                    dest = key ^ ((K)3 << (P + ns - 1));
+                    dest = key ^ O::shl((K)3, P + ns - 1);
                 }
             } else {
                 if (P == 0) {  // mode 0 -> last mode
                     const K z = ~key & O::low(nb);
                     nt = nb - 1 - (O::W - 1 - clz_k(z));
-                    dest = (key >> 1) | O::bit(nb - 1);
+                    dest = O::shr(key, 1) | O::bit(nb - 1);
                 } else {
                     const K z = ~key & O::low(P - 1);
                     nt = z ? (P - 2 - (O::W - 1 - clz_k(z))) : (P - 1);
-                    dest = key ^ ((K)3 << (P - 1));
+                    dest = key ^ O::shl((K)3, P - 1);
                 }
             }
             if constexpr (sizeof(V) == 4) val = __ldg(p.hop32_tab + ns * (nt + 1));
@@ -266,11 +293,11 @@ template <int KIND> struct RealModel {
         K dest;
         if (s2 == s + 1) {
             nt = run_from(key, P + ns + 1);
-            dest = key ^ ((K)3 << (P + ns - 1));
+            dest = key ^ O::shl((K)3, P + ns - 1);
         } else if (s2 == s - 1) {
             const K z = ~key & O::low(P - 1);
             nt = z ? (P - 2 - (O::W - 1 - clz_k(z))) : (P - 1);
-            dest = key ^ ((K)3 << (P - 1));
+            dest = key ^ O::shl((K)3, P - 1);
         } else {
             const int q = mode_start(key, s2);
             nt = run_from(key, q);

@@ -1272,6 +1272,28 @@ __global__ void __launch_bounds__(BLOCK) k_shift(const RunDesc* __restrict__ run
     RunState* st = R->st;
     __shared__ double s_S;
     __shared__ int s_ok;
+    __shared__ double s_h[BLOCK], s_v[BLOCK];
+    // the projected-energy partials of the reference buckets: strided over
+    // the block, then a tree in a fixed order (the result does not depend on
+    // timing)
+    {
+        double hp = 0.0, vp = 0.0;
+        for (unsigned i = threadIdx.x; i < R->n_ref_bkt; i += BLOCK) {
+            const unsigned b = R->ref_bkt[i];
+            hp += R->part_h[b];
+            vp += R->part_v[b];
+        }
+        s_h[threadIdx.x] = hp;
+        s_v[threadIdx.x] = vp;
+        __syncthreads();
+        for (int o = BLOCK / 2; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) {
+                s_h[threadIdx.x] += s_h[threadIdx.x + o];
+                s_v[threadIdx.x] += s_v[threadIdx.x + o];
+            }
+            __syncthreads();
+        }
+    }
     if (threadIdx.x == 0) {
         s_ok = 0;
         if (!*(volatile unsigned*)&st->err) {
@@ -1279,11 +1301,7 @@ __global__ void __launch_bounds__(BLOCK) k_shift(const RunDesc* __restrict__ run
             if (R->mode_det) nrm = st->norm_fp;
             else nrm = fixed_to_double(st->norm_lo, st->norm_hi, R->norm_q);
             const unsigned long long len = st->len_acc;
-            double hp = 0.0, vp = 0.0;
-            for (unsigned i = 0; i < R->n_ref_bkt; ++i) {
-                hp += R->part_h[R->ref_bkt[i]];
-                vp += R->part_v[R->ref_bkt[i]];
-            }
+            const double hp = s_h[0], vp = s_v[0];
             if (nrm == 0.0 || len == 0) {
                 st->err |= FQ_DERR_EMPTY;
             } else {
