@@ -214,6 +214,21 @@ __device__ __forceinline__ unsigned segment_of(uint64_t mixed, int log2B) {
 
 template <int KIND> struct Model;
 
+// neighbour of site s = x + Lx y of the periodic Lx x Ly lattice in direction
+// d = +x, -x, +y, -y, computed in registers (the neighbour table in device
+// memory put a dependent load into every hop's chain); y = floor(s / Lx) by
+// a multiply and shift, exact for s < 128 and Lx <= 128
+__device__ __forceinline__ int neighbour2d(const ModelParams& p, int s, int d) {
+    const int Lx = p.Lx, Ly = p.Ly;
+    const int y = (int)(((unsigned)s * p.lx_magic) >> 16);
+    const int x = s - y * Lx;
+    const int xp = x + 1 == Lx ? s - x : s + 1;
+    const int xm = x == 0 ? s + Lx - 1 : s - 1;
+    const int yp = y + 1 == Ly ? x : s + Lx;
+    const int ym = y == 0 ? x + (Ly - 1) * Lx : s - Lx;
+    return d == 0 ? xp : d == 1 ? xm : d == 2 ? yp : ym;
+}
+
 // Real space (Eq. bose-hubbard-hamiltonian): H_ii = (u/2) sum n(n-1); each
 // (direction, occupied site) pair hops one boson to a neighbour with value
 // -t sqrt(n_s (n_s' + 1)).  Entry k: direction k / n_occ, occupied site
@@ -293,7 +308,7 @@ template <int KIND> struct RealModel {
         typedef KeyOps<K> O;
         const int s = P - O::popc(key & O::low(P));
         const int ns = run_from(key, P);
-        const int s2 = p.nbr[d][s];
+        const int s2 = neighbour2d(p, s, d);
         const int q = mode_start(key, s2);
         const int nt = run_from(key, q);
         const K dest = ins_one(del_bit(key, P), q - (s2 > s ? 1 : 0));
