@@ -74,6 +74,9 @@ def ratio_estimate(num, den, confidence: float = 0.99) -> dict:
     da, db = ba - ba.mean(), bb - bb.mean()
     va, vb, cab = np.dot(da, da) / n / n, np.dot(db, db) / n / n, np.dot(da, db) / n / n
     A, B = a.mean(), b.mean()
+    if B == 0.0:
+        return dict(ratio=float("nan"), err=float("inf"), k=j + 1, ok=False)
     r = A / B
-    var = r * r * (va / (A * A) + vb / (B * B) - 2.0 * cab / (A * B))
+    # r^2 (va/A^2 + vb/B^2 - 2 cab/(A B)) with A divided out, so A = 0 is fine
+    var = (va - 2.0 * r * cab + r * r * vb) / (B * B)
     return dict(ratio=float(r), err=float(np.sqrt(max(var, 0.0))), k=j + 1, ok=ok)

@@ -325,7 +325,6 @@ extern "C" int fq_ham_create(fq_ham** out, int kind, int Lx, int Ly, int N, doub
         // directions (+x, -x, +y, -y) on the periodic lattice, site x + Lx y
         for (int s2 = 0; s2 < M; ++s2) {
             const int x = s2 % Lx, y = s2 / Lx;
-            mp.lx_magic = (65536u + (unsigned)Lx - 1u) / (unsigned)Lx;
             mp.nbr[0][s2] = (unsigned char)((x + 1) % Lx + Lx * y);
             mp.nbr[1][s2] = (unsigned char)((x + Lx - 1) % Lx + Lx * y);
             mp.nbr[2][s2] = (unsigned char)(x + Lx * ((y + 1) % Ly));

@@ -79,10 +79,12 @@ template <> struct KeyOps<u128> {
     __device__ __forceinline__ static int popc(u128 k) {
         return __popcll((uint64_t)k) + __popcll((uint64_t)(k >> 64));
     }
+    // the word is selected first, so one 64-bit search runs
     __device__ __forceinline__ static int nth(u128 k, int j) {
-        uint64_t lo = (uint64_t)k;
-        int c = __popcll(lo);
-        return j < c ? nth_set64(lo, j) : 64 + nth_set64((uint64_t)(k >> 64), j - c);
+        const uint64_t lo = (uint64_t)k, hi = (uint64_t)(k >> 64);
+        const int c = __popcll(lo);
+        const bool in_lo = j < c;
+        return (in_lo ? 0 : 64) + nth_set64(in_lo ? lo : hi, in_lo ? j : j - c);
     }
     // s >= 0; every 64-bit shift below is by 0..63 and the cases are
     // selected, not branched to (lanes of a warp take different amounts)
@@ -108,10 +110,9 @@ template <> struct KeyOps<u128> {
         return make(p >= 64 ? ~0ull : m, p >= 128 ? ~0ull : (p >= 64 ? m : 0ull));
     }
     __device__ __forceinline__ static int ctz(u128 x) {
-        uint64_t lo = (uint64_t)x, hi = (uint64_t)(x >> 64);
-        if (lo) return __ffsll((long long)lo) - 1;
-        if (hi) return 64 + __ffsll((long long)hi) - 1;
-        return 128;
+        const uint64_t lo = (uint64_t)x, hi = (uint64_t)(x >> 64);
+        const int a = __ffsll((long long)lo) - 1, b = __ffsll((long long)hi) - 1;
+        return lo ? a : (hi ? 64 + b : 128);
     }
     __device__ __forceinline__ static u128 bit(int p) {
         const uint64_t b = 1ull << (p & 63);
@@ -148,6 +149,17 @@ template <class K> __device__ __forceinline__ K del_bit(K x, int p) {
 template <class K> __device__ __forceinline__ K ins_one(K x, int p) {
     typedef KeyOps<K> O;
     return (x & O::low(p)) | O::bit(p) | O::shl(O::shr(x, p), p + 1);
+}
+// ins_one(del_bit(k, P), qq) in one step: the one-bit at P moves to qq (a
+// position counted after the removal) and only the bits between them shift
+// by one -- down when qq > P, up when qq < P
+template <class K> __device__ __forceinline__ K move_one(K k, int P, int qq) {
+    typedef KeyOps<K> O;
+    const int lo = P < qq ? P : qq, hi = P < qq ? qq : P;
+    const K M = O::low(hi + 1) ^ O::low(lo);
+    const K sh = qq > P ? (k >> 1) : (k << 1);
+    const K b = O::bit(qq);
+    return (k & ~M) | (sh & M & ~b) | b;
 }
 template <class K> __device__ __forceinline__ K remove_boson(K k, int s) {
     return del_bit(k, mode_start(k, s));
@@ -213,21 +225,6 @@ __device__ __forceinline__ unsigned segment_of(uint64_t mixed, int log2B) {
 // Hamiltonians
 
 template <int KIND> struct Model;
-
-// neighbour of site s = x + Lx y of the periodic Lx x Ly lattice in direction
-// d = +x, -x, +y, -y, computed in registers (the neighbour table in device
-// memory put a dependent load into every hop's chain); y = floor(s / Lx) by
-// a multiply and shift, exact for s < 128 and Lx <= 128
-__device__ __forceinline__ int neighbour2d(const ModelParams& p, int s, int d) {
-    const int Lx = p.Lx, Ly = p.Ly;
-    const int y = (int)(((unsigned)s * p.lx_magic) >> 16);
-    const int x = s - y * Lx;
-    const int xp = x + 1 == Lx ? s - x : s + 1;
-    const int xm = x == 0 ? s + Lx - 1 : s - 1;
-    const int yp = y + 1 == Ly ? x : s + Lx;
-    const int ym = y == 0 ? x + (Ly - 1) * Lx : s - Lx;
-    return d == 0 ? xp : d == 1 ? xm : d == 2 ? yp : ym;
-}
 
 // Real space (Eq. bose-hubbard-hamiltonian): H_ii = (u/2) sum n(n-1); each
 // (direction, occupied site) pair hops one boson to a neighbour with value
@@ -308,10 +305,10 @@ template <int KIND> struct RealModel {
         typedef KeyOps<K> O;
         const int s = P - O::popc(key & O::low(P));
         const int ns = run_from(key, P);
-        const int s2 = neighbour2d(p, s, d);
+        const int s2 = p.nbr[d][s];  // the table load measured faster than computing it
         const int q = mode_start(key, s2);
         const int nt = run_from(key, q);
-        const K dest = ins_one(del_bit(key, P), q - (s2 > s ? 1 : 0));
+        const K dest = move_one(key, P, q - (s2 > s ? 1 : 0));
         // -(t sqrt(n_s (n_s' + 1))) from the table
         if constexpr (sizeof(V) == 4) val = __ldg(p.hop32_tab + ns * (nt + 1));
         else val = __ldg(p.hop_tab + ns * (nt + 1));

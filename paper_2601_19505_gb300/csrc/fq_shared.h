@@ -42,7 +42,6 @@ struct ModelParams {
     const float* hop32_tab;          // (float) of hop_tab
     double eps[FQ_MAX_MOM_MODES];    // momentum-space single-particle energies
     unsigned char nbr[4][128];       // real space: neighbour of site s in direction d
-    unsigned lx_magic;               // ceil(2^16 / Lx): y = (s lx_magic) >> 16 for s < 128
 };
 
 // One row of the time series; layout identical to fq_stats in fciqmc.h.
