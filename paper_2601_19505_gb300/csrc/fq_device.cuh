@@ -150,17 +150,6 @@ template <class K> __device__ __forceinline__ K ins_one(K x, int p) {
     typedef KeyOps<K> O;
     return (x & O::low(p)) | O::bit(p) | O::shl(O::shr(x, p), p + 1);
 }
-// ins_one(del_bit(k, P), qq) in one step: the one-bit at P moves to qq (a
-// position counted after the removal) and only the bits between them shift
-// by one -- down when qq > P, up when qq < P
-template <class K> __device__ __forceinline__ K move_one(K k, int P, int qq) {
-    typedef KeyOps<K> O;
-    const int lo = P < qq ? P : qq, hi = P < qq ? qq : P;
-    const K M = O::low(hi + 1) ^ O::low(lo);
-    const K sh = qq > P ? (k >> 1) : (k << 1);
-    const K b = O::bit(qq);
-    return (k & ~M) | (sh & M & ~b) | b;
-}
 template <class K> __device__ __forceinline__ K remove_boson(K k, int s) {
     return del_bit(k, mode_start(k, s));
 }
@@ -301,14 +290,23 @@ template <int KIND> struct RealModel {
         // one-bit at P and insert one at the start q of the target run,
         // located by a search from bit 0 (one code path measured 8 % faster
         // than separator swaps for neighbours along x and this path for the
-        // rest)
+        // rest).  Bits below P and below q, computed once, give the mode
+        // index, both run lengths (the first zero at or above a run's start)
+        // and the moved stretch: [P, q) rotates down by one when s' > s,
+        // [q, P] up by one when s' < s, the boson landing at its far end.
         typedef KeyOps<K> O;
-        const int s = P - O::popc(key & O::low(P));
-        const int ns = run_from(key, P);
+        const K lowP = O::low(P), nk = ~key;
+        const int s = P - O::popc(key & lowP);
+        const int ns = O::ctz(nk & ~lowP) - P;
         const int s2 = p.nbr[d][s];  // the table load measured faster than computing it
         const int q = mode_start(key, s2);
-        const int nt = run_from(key, q);
-        const K dest = move_one(key, P, q - (s2 > s ? 1 : 0));
+        const K lowq = O::low(q);
+        const int nt = O::ctz(nk & ~lowq) - q;
+        const bool up = s2 > s;
+        const K Mu = lowq ^ lowP;
+        const K M = up ? Mu : (Mu | O::bit(P));
+        const K sh = up ? (key >> 1) : (key << 1);
+        const K dest = (key & ~M) | (sh & M) | O::bit(q - (up ? 1 : 0));
         // -(t sqrt(n_s (n_s' + 1))) from the table
         if constexpr (sizeof(V) == 4) val = __ldg(p.hop32_tab + ns * (nt + 1));
         else val = __ldg(p.hop_tab + ns * (nt + 1));
