@@ -168,7 +168,7 @@ __device__ __forceinline__ void warp_copy_async(void* dst, const void* src, unsi
 // atomics' latency overlaps the next round's work.  No block barriers.
 
 // dynamic shared memory of one spawn warp
-template <class K, int AMP, int CH> struct SpawnSmem {
+template <class K, int AMP, int CH, int KIND> struct SpawnSmem {
     typedef typename AmpT<AMP>::A A;
     typedef typename AmpT<AMP>::C CO;
     static constexpr size_t al(size_t b) { return (b + 15) / 16 * 16; }
@@ -177,7 +177,11 @@ template <class K, int AMP, int CH> struct SpawnSmem {
     static constexpr size_t coef_off = amp_off + al(2 * CH * sizeof(A));  // CO [CH]
     static constexpr size_t off_off = coef_off + al(CH * sizeof(CO));     // unsigned [CH + 1]
     static constexpr size_t m_off = off_off + al((CH + 1) * sizeof(unsigned));  // unsigned [CH]
-    static constexpr size_t bytes = m_off + al(CH * sizeof(unsigned));
+    // the run's model parameters (the part the model's column reads)
+    static constexpr size_t mp_bytes =
+        KIND == FQ_KIND_MOM_1D ? sizeof(ModelParams) : offsetof(ModelParams, eps);
+    static constexpr size_t mp_off = m_off + al(CH * sizeof(unsigned));
+    static constexpr size_t bytes = mp_off + al(mp_bytes);
 };
 
 template <class K, int AMP, int KIND, int V, int IPT>
@@ -189,7 +193,7 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     typedef typename AmpT<AMP>::C CO;
     typedef Model<KIND> MD;
     typedef typename MD::Col Col;
-    typedef SpawnSmem<K, AMP, 32 * IPT> SM;
+    typedef SpawnSmem<K, AMP, 32 * IPT, KIND> SM;
     constexpr int CH = 32 * IPT;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -199,6 +203,12 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     CO* const wcoef = (CO*)(wbase + SM::coef_off);
     unsigned* const woff = (unsigned*)(wbase + SM::off_off);
     unsigned* const wm = (unsigned*)(wbase + SM::m_off);
+    // the current run's model parameters, copied into the warp's shared
+    // memory when the run is entered: read there, they are not reloaded
+    // through L1 after every spawn store (which the compiler cannot tell
+    // apart from the run descriptor)
+    ModelParams* const wmp = (ModelParams*)(wbase + SM::mp_off);
+    const ModelParams& mp = *wmp;
     unsigned g0, g1;
     warp_range(G, blockIdx.x * WPB + wib, gridDim.x * WPB, g0, g1);
 
@@ -218,6 +228,10 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     double dt = 0.0;
     uint2 rkey = make_uint2(0, 0);
     int early = 0;
+    // per-source constants of the run, in registers for the same reason
+    int r_det = 0, r_trel_one = 0, r_mmax = 0;
+    double r_trel = 0.0;
+    const typename AmpT<AMP>::C* r_coef = nullptr;
     unsigned n_ex = 0, n_inex = 0, n_sp = 0;
 
     // the spawn whose bucket slot is being reserved (stored one spawn later)
@@ -276,6 +290,16 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
         stepno = (unsigned)(R->st->step + 1);
         rkey = make_uint2(R->key_x, R->key_y);
         early = R->early;
+        r_det = R->mode_det;
+        r_trel_one = R->trel_one;
+        r_trel = R->t_rel;
+        r_mmax = R->mmax;
+        if constexpr (AMP == FQ_AMP_F32) r_coef = R->coef32;
+        else if constexpr (AMP == FQ_AMP_F64) r_coef = R->coef64;
+        __syncwarp();  // every lane is done with the previous run's parameters
+        for (unsigned i = (unsigned)lane; i < (unsigned)(SM::mp_bytes / 4); i += 32u)
+            ((unsigned*)wmp)[i] = ((const unsigned*)&R->mp)[i];
+        __syncwarp();
     };
     // the next non-empty segment of the current run at or after g; the end
     // of the run's part of the range if none (n = its entry count)
@@ -301,7 +325,6 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     // rounds to nothing
     auto make_col = [&](K key, const Col& col, CO cf, unsigned mm, unsigned a, K& dest,
                         S& val) -> bool {
-        const ModelParams& mp = R->mp;
         const unsigned m = mm & 0x3FFFFFFFu;
         const bool ex = (AMP != FQ_AMP_INT) && (mm >> 31);
         uint4 w = make_uint4(0, 0, 0, 0);
@@ -336,7 +359,7 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     auto make = [&](K key, CO cf, unsigned mm, unsigned a, K& dest, S& val) -> bool {
         Col col;
         if constexpr (KIND != FQ_KIND_MOM_1D) col.n_occ = (int)((mm & 0x3FFFFFFFu) / (unsigned)MD::Z);
-        else MD::num_offdiag(R->mp, key, col);
+        else MD::num_offdiag(mp, key, col);
         return make_col(key, col, cf, mm, a, dest, val);
     };
 
@@ -393,7 +416,6 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
 
         const K* wkey = in_key + b * CH;
         const A* wamp = in_amp + b * CH;
-        const ModelParams& mp = R->mp;
         // sources i = j * 32 + lane: the decision, the coefficient and the
         // first attempt at once; further attempts are counted (extras) and
         // dealt out below
@@ -419,21 +441,20 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
                     mm = m | (c < (CO)0 ? 0x40000000u : 0u);
                 } else {
                     bool ex;
-                    if (R->mode_det) ex = true;
-                    else if (R->trel_one) ex = fl >= m;  // |c| >= m for an integer m
-                    else ex = fabs((double)c) * R->t_rel >= (double)m;
+                    if (r_det) ex = true;
+                    else if (r_trel_one) ex = fl >= m;  // |c| >= m for an integer m
+                    else ex = fabs((double)c) * r_trel >= (double)m;
                     cnt = ex ? m : ce;
                     if (ex) {
                         ++n_ex;
                         cf = (-(CO)dt) * c;
                     } else {
                         ++n_inex;
-                        const int mmax = R->mmax;
+                        const int mmax = r_mmax;
                         if (KIND != FQ_KIND_MOM_1D && (int)m <= mmax && (int)ce <= mmax) {
                             // (-dt) (m / n) from the run's table for this dt
                             const size_t ri = (size_t)m * (size_t)(mmax + 1) + ce;
-                            if constexpr (AMP == FQ_AMP_F32) cf = R->coef32[ri] * c;
-                            else cf = R->coef64[ri] * c;
+                            cf = __ldg(r_coef + ri) * c;
                         } else {
                             cf = ((-(CO)dt) * ((CO)m / (CO)ce)) * c;
                         }
@@ -541,10 +562,38 @@ __device__ __forceinline__ int table_find(const K* tkey, unsigned mask, K key) {
     return -1;
 }
 
+// The run's constants that Pi, the norm terms and the diagonal term read for
+// every value, taken once per bucket: read from the run descriptor inside
+// the loops they would be loaded again after every store of the compacted
+// vector, which the compiler cannot tell apart from the descriptor.
+// Seven registers: theta's bits, (float)theta, theta's exponent, two flags
+// and the diagonal-factor table of the amplitude type.
+struct StepConst {
+    unsigned long long theta_bits;  // dbits(theta)
+    float theta32;                  // (float)theta
+    int theta_exp;
+    int flags;                      // 1: theta is a power of two, 2: deterministic limit
+    const void* diag;               // fac64 (FP64, integer walkers) or del32 (FP32)
+    __device__ __forceinline__ double theta() const { return bdouble(theta_bits); }
+    __device__ __forceinline__ bool pow2() const { return flags & 1; }
+    __device__ __forceinline__ bool det() const { return flags & 2; }
+};
+template <int AMP>
+__device__ __forceinline__ StepConst step_const(const RunDesc* R) {
+    StepConst k;
+    k.theta_bits = dbits(R->theta);
+    k.theta32 = R->theta32;
+    k.theta_exp = R->theta_exp;
+    k.flags = (R->theta_pow2 ? 1 : 0) | (R->mode_det ? 2 : 0);
+    if constexpr (AMP == FQ_AMP_F32) k.diag = R->del32;
+    else k.diag = R->fac64;
+    return k;
+}
+
 // Pi (Eq. vec-compression) of one merged value: keep |w| >= theta, else
 // sign(w) theta with probability |w| / theta.  `out` is the stored value.
 template <int AMP>
-__device__ __forceinline__ bool compress(typename AmpT<AMP>::ACC w, const RunDesc* R, uint2 rkey,
+__device__ __forceinline__ bool compress(typename AmpT<AMP>::ACC w, const StepConst& R, uint2 rkey,
                                          unsigned stepno, uint64_t h,
                                          typename AmpT<AMP>::ACC& out) {
     typedef typename AmpT<AMP>::ACC ACC;
@@ -553,19 +602,19 @@ __device__ __forceinline__ bool compress(typename AmpT<AMP>::ACC w, const RunDes
         return w != 0;
     } else {
         const unsigned long long ab = abs_dbits(w);
-        if (R->mode_det) {
+        if (R.det()) {
             out = w;
             return ab != 0;
         }
         if (ab == 0) return false;
-        const double theta = R->theta;
-        if (R->theta_pow2) {
+        const double theta = R.theta();
+        if (R.pow2()) {
             if (ab >= dbits(theta)) {
                 out = w;
                 return true;
             }
             const uint4 r = draw(rkey, stepno, 0xFFFFFFFFu, h);
-            if (!below_scaled(u53_of(r), ab, R->theta_exp)) return false;
+            if (!below_scaled(u53_of(r), ab, R.theta_exp)) return false;
         } else {
             const double aw = bdouble(ab);
             if (aw >= theta) {
@@ -579,7 +628,7 @@ __device__ __forceinline__ bool compress(typename AmpT<AMP>::ACC w, const RunDes
         if constexpr (AMP == FQ_AMP_F64)
             out = bdouble(dbits(theta) | (dbits(w) & 0x8000000000000000ull));
         else
-            out = __uint_as_float(__float_as_uint(R->theta32) | (__float_as_uint(w) & 0x80000000u));
+            out = __uint_as_float(__float_as_uint(R.theta32) | (__float_as_uint(w) & 0x80000000u));
         return true;
     }
 }
@@ -597,26 +646,34 @@ struct MergeAcc {
 // early-comp), where the draw is the one of the spawn or a stream of its own:
 // |v| >= theta (kept as it is), decided on the bits
 template <class V>
-__device__ __forceinline__ bool at_least_theta(V v, const RunDesc* R) {
+__device__ __forceinline__ bool at_least_theta(V v, const StepConst& k) {
     const unsigned long long ab = abs_dbits(v);
-    return R->theta_pow2 ? ab >= dbits(R->theta) : bdouble(ab) >= R->theta;
+    return k.pow2() ? ab >= k.theta_bits : bdouble(ab) >= k.theta();
+}
+template <class V>
+__device__ __forceinline__ bool at_least_theta(V v, const RunDesc* R) {
+    return at_least_theta(v, step_const<FQ_AMP_F64>(R));  // the table is not read
 }
 // |v| < theta: v becomes sign(v) theta with probability |v| / theta (the
 // 53-bit uniform of r against |v| / theta), else it is dropped (false)
 template <class V>
-__device__ __forceinline__ bool pi_below(V& v, uint4 r, const RunDesc* R) {
+__device__ __forceinline__ bool pi_below(V& v, uint4 r, const StepConst& k) {
     const unsigned long long ab = abs_dbits(v);
     if (ab == 0) return false;
-    if (R->theta_pow2) {
-        if (!below_scaled(u53_of(r), ab, R->theta_exp)) return false;
+    if (k.pow2()) {
+        if (!below_scaled(u53_of(r), ab, k.theta_exp)) return false;
     } else {
-        if (!(uniform53(r) < bdouble(ab) / R->theta)) return false;
+        if (!(uniform53(r) < bdouble(ab) / k.theta())) return false;
     }
     if constexpr (sizeof(V) == 8)
-        v = bdouble(dbits(R->theta) | (dbits(v) & 0x8000000000000000ull));
+        v = bdouble(k.theta_bits | (dbits(v) & 0x8000000000000000ull));
     else
-        v = __uint_as_float(__float_as_uint(R->theta32) | (__float_as_uint(v) & 0x80000000u));
+        v = __uint_as_float(__float_as_uint(k.theta32) | (__float_as_uint(v) & 0x80000000u));
     return true;
+}
+template <class V>
+__device__ __forceinline__ bool pi_below(V& v, uint4 r, const RunDesc* R) {
+    return pi_below(v, r, step_const<FQ_AMP_F64>(R));  // the table is not read
 }
 
 // add a warp's share of one run's step totals to the run's accumulators
@@ -669,7 +726,7 @@ __device__ __forceinline__ bool is_taken(long long x) {
 // compaction and the norm terms of the values a warp keeps (keep: the lane
 // stores `out` at `key`)
 template <class K, int AMP>
-__device__ __forceinline__ void merge_store(const RunDesc* R, bool keep, K key,
+__device__ __forceinline__ void merge_store(const StepConst& R, bool keep, K key,
                                             typename AmpT<AMP>::ACC out, K* __restrict__ ok,
                                             typename AmpT<AMP>::A* __restrict__ oa, unsigned Cv,
                                             int nq, int det, int lane, unsigned& nout,
@@ -691,7 +748,7 @@ __device__ __forceinline__ void merge_store(const RunDesc* R, bool keep, K key,
         } else {
             if (det) {
                 acc.nfp += fabs((double)out);
-            } else if (R->theta_pow2 && abs_dbits(out) == dbits(R->theta)) {
+            } else if (R.pow2() && abs_dbits(out) == R.theta_bits) {
                 ++acc.ntheta;  // theta = 2^(nq + 52): 2^52 units, added at the flush
             } else {
                 unsigned long long lo, hi;
@@ -704,7 +761,7 @@ __device__ __forceinline__ void merge_store(const RunDesc* R, bool keep, K key,
 }
 
 template <class K, int AMP>
-__device__ __forceinline__ void merge_emit(const RunDesc* R, bool has, K key,
+__device__ __forceinline__ void merge_emit(const StepConst& R, bool has, K key,
                                            typename AmpT<AMP>::ACC w, uint2 rkey, unsigned stepno,
                                            K* __restrict__ ok, typename AmpT<AMP>::A* __restrict__ oa,
                                            unsigned Cv, int nq, int det, int early, int lane,
@@ -755,20 +812,20 @@ __device__ __forceinline__ void bucket_finish(const RunDesc* R, unsigned seg, un
 // with the draw of stream 0xFFFFFFFE); under early compression it is then
 // compressed alone with the draw of stream 0xFFFFFFFD (0 when dropped).
 template <class K, int AMP, int KIND>
-__device__ __forceinline__ typename AmpT<AMP>::ACC diag_term(const RunDesc* R, K key,
-                                                            typename AmpT<AMP>::A c, uint2 rkey,
-                                                            unsigned stepno, int early) {
+__device__ __forceinline__ typename AmpT<AMP>::ACC diag_term(const RunDesc* R, const StepConst& kc,
+                                                            K key, typename AmpT<AMP>::A c,
+                                                            uint2 rkey, unsigned stepno, int early) {
     typedef typename AmpT<AMP>::ACC ACC;
     typedef Model<KIND> MD;
     ACC w;
     if constexpr (KIND != FQ_KIND_MOM_1D) {
         const int si = MD::diag_index(key);
         if constexpr (AMP == FQ_AMP_F32) {
-            w = c + c * __ldg(R->del32 + si);
+            w = c + c * __ldg((const float*)kc.diag + si);
         } else if constexpr (AMP == FQ_AMP_F64) {
-            w = c * __ldg(R->fac64 + si);
+            w = c * __ldg((const double*)kc.diag + si);
         } else {
-            const double x = (double)c * __ldg(R->fac64 + si);
+            const double x = (double)c * __ldg((const double*)kc.diag + si);
             const double fl = floor(x);
             const uint4 r4 = draw(rkey, stepno, 0xFFFFFFFEu, KeyOps<K>::rng_h(key));
             w = (ACC)((long long)fl + (uniform53(r4) < x - fl ? 1 : 0));
@@ -788,9 +845,9 @@ __device__ __forceinline__ typename AmpT<AMP>::ACC diag_term(const RunDesc* R, K
         }
     }
     if constexpr (AMP != FQ_AMP_INT) {
-        if (early && !at_least_theta(w, R)) {
+        if (early && !at_least_theta(w, kc)) {
             const uint4 r4 = draw(rkey, stepno, 0xFFFFFFFDu, KeyOps<K>::rng_h(key));
-            if (!pi_below(w, r4, R)) w = (ACC)0;
+            if (!pi_below(w, r4, kc)) w = (ACC)0;
         }
     }
     return w;
@@ -825,6 +882,7 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
     const int nq = R->norm_q;
     const int det = R->mode_det;
     const int early = R->early;
+    const StepConst kc = step_const<AMP>(R);
 
     // annihilation: every spawn to the bucket adds into its address; new
     // addresses join the list in warp order.  The next spawns are loaded
@@ -881,7 +939,7 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
             ACC w = (ACC)0;
             const bool has = i < n_old;
             if (has) {
-                w = diag_term<K, AMP, KIND>(R, key, c, rkey, stepno, early);
+                w = diag_term<K, AMP, KIND>(R, kc, key, c, rkey, stepno, early);
                 if (n_sp) {
                     const int q = table_find(tk, mask, key);
                     if (q >= 0) {
@@ -890,8 +948,8 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
                     }
                 }
             }
-            merge_emit<K, AMP>(R, has, key, w, rkey, stepno, ok, oa, Cv, nq, det, early, lane, nout,
-                              acc);
+            merge_emit<K, AMP>(kc, has, key, w, rkey, stepno, ok, oa, Cv, nq, det, early, lane,
+                               nout, acc);
         }
     }
     __syncwarp();
@@ -907,8 +965,8 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
             has = !is_taken(w);
             key = tk[q];
         }
-        merge_emit<K, AMP>(R, has, key, w, rkey, stepno, ok, oa, Cv, nq, det, early, lane, nout,
-                              acc);
+        merge_emit<K, AMP>(kc, has, key, w, rkey, stepno, ok, oa, Cv, nq, det, early, lane, nout,
+                           acc);
     }
     __syncwarp();
     bucket_finish<K, AMP>(R, seg, cur, nout, ok, oa, lane);
@@ -970,6 +1028,7 @@ __device__ __forceinline__ void sort_bucket(const RunDesc* R, unsigned seg, unsi
     const unsigned stepno = (unsigned)(R->st->step + 1);
     const uint2 rkey = make_uint2(R->key_x, R->key_y);
     const int nq = R->norm_q, det = R->mode_det, early = R->early;
+    const StepConst kc = step_const<AMP>(R);
     K* const wk = (K*)ws;
     ACC* const wv = (ACC*)(ws + L::val_off(C));
     unsigned short* const wh = (unsigned short*)(ws + L::hash_off(C));
@@ -981,7 +1040,7 @@ __device__ __forceinline__ void sort_bucket(const RunDesc* R, unsigned seg, unsi
     for (unsigned i = lane; i < n_old; i += 32) {
         const K key = vk[i];
         wk[i] = key;
-        wv[i] = diag_term<K, AMP, KIND>(R, key, va[i], rkey, stepno, early);
+        wv[i] = diag_term<K, AMP, KIND>(R, kc, key, va[i], rkey, stepno, early);
         wh[i] = hash16(key);
         ia[i] = (unsigned short)i;
     }
@@ -1058,7 +1117,7 @@ __device__ __forceinline__ void sort_bucket(const RunDesc* R, unsigned seg, unsi
                 }
             }
         }
-        merge_emit<K, AMP>(R, head, key, w, rkey, stepno, ok, oa, Cv, nq, det, early, lane, nout,
+        merge_emit<K, AMP>(kc, head, key, w, rkey, stepno, ok, oa, Cv, nq, det, early, lane, nout,
                            acc);
     }
     __syncwarp();
@@ -1682,7 +1741,7 @@ __global__ void __launch_bounds__(128) k_gs_axpy(const RunDesc* __restrict__ run
                     }
                 }
             }
-            merge_store<K, AMP>(R, keep, key, w, kk, ka, Cv, nq, det, lane, nout, acc);
+            merge_store<K, AMP>(step_const<AMP>(R), keep, key, w, kk, ka, Cv, nq, det, lane, nout, acc);
         }
         __syncwarp();
         bucket_finish<K, AMP>(R, seg, cur, nout, kk, ka, lane);

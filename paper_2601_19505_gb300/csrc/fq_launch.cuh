@@ -13,7 +13,7 @@ template <class K, int AMP, int KIND> struct Launch {
     typedef typename AmpT<AMP>::ACC ACC;
 
     static constexpr size_t spawn_smem(int wpb) {
-        return (size_t)wpb * SpawnSmem<K, AMP, 128>::bytes;
+        return (size_t)wpb * SpawnSmem<K, AMP, 128, KIND>::bytes;
     }
     template <int V> static void spawn_v(const LaunchCfg& c, const RunDesc* d, const unsigned* sr,
                                          unsigned G, cudaStream_t s) {

@@ -40,8 +40,10 @@ struct ModelParams {
     const double* sqrt_tab;          // sqrt((double)k), k <= kmax (device)
     const double* hop_tab;           // -(t * sqrt((double)k)), k <= kmax (device)
     const float* hop32_tab;          // (float) of hop_tab
-    double eps[FQ_MAX_MOM_MODES];    // momentum-space single-particle energies
     unsigned char nbr[4][128];       // real space: neighbour of site s in direction d
+    // kept last: the spawn kernel copies the members before it for real-space
+    // models and the whole struct for momentum space
+    double eps[FQ_MAX_MOM_MODES];    // momentum-space single-particle energies
 };
 
 // One row of the time series; layout identical to fq_stats in fciqmc.h.
