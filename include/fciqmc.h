@@ -251,7 +251,13 @@ int fq_run_sample(fq_run *r, uint64_t seed, size_t want, fq_key *keys, double *a
 int fq_run_spawns(fq_run *r, fq_key *dest, double *val, size_t cap, size_t *n);
 /* Grow the vector and spawn capacities to at least these totals (never
  * shrinks), keeping the vector.  The usual answer to FQ_ERR_CAPACITY: the
- * run was rolled back, so grow and step again.  Synchronises. */
+ * run was rolled back, so grow and step again.  The vector's new buffers
+ * are allocated while the old ones still hold it; the spawn buffers hold
+ * nothing between steps and are released before their successors are
+ * allocated.  FQ_ERR_NOMEM when the device memory cannot hold the new
+ * sizes: the run keeps what it had (the spawn buffers are allocated again
+ * at their old size; should even that fail, every later step and check of
+ * the run returns FQ_ERR_NOMEM).  Synchronises. */
 int fq_run_reserve(fq_run *r, size_t capacity_vec, size_t capacity_spawn);
 /* Current total capacities (entries of the vector, spawns per step). */
 int fq_run_capacity(const fq_run *r, size_t *capacity_vec, size_t *capacity_spawn);
@@ -265,6 +271,18 @@ int fq_run_capacity(const fq_run *r, size_t *capacity_vec, size_t *capacity_spaw
  * within 200 KB of shared memory; scratch_slots <= 2^26); 0 restores the
  * default.  Synchronises; the next step rebuilds the launch. */
 int fq_run_set_tables(fq_run *r, unsigned slots, unsigned scratch_slots);
+/* Spawn-buffer layout (tests and tuning; not in the paper).  The first
+ * `primary` slots of every spawn bucket lie in one dense region of the spawn
+ * buffers, the bucket's other slots in a second region after it; a spawn is
+ * stored in the first free slot of its bucket either way, so the results do
+ * not depend on the split.  Spawns land in random buckets, and a small dense
+ * region keeps their stores on few memory pages.  By default `primary` is
+ * the steady-state bucket fill (spawns per step ~ 1.1 N_t / threshold) plus
+ * three standard deviations, rounded up to a multiple of 32.  `primary` must
+ * be a multiple of 32 and at most the bucket capacity (0: every slot in the
+ * second region); else FQ_ERR_INVALID.  A later fq_run_reserve keeps it.
+ * Synchronises. */
+int fq_run_set_spawn_split(fq_run *r, unsigned primary);
 /* Buckets the merge summed in the on-chip table and in the scratch table
  * since the run was seeded (a rolled-back step's buckets included).
  * Synchronises. */

@@ -78,6 +78,7 @@ SYMBOLS = {
     "fq_run_reserve": (C.c_int, [C.c_void_p, C.c_size_t, C.c_size_t]),
     "fq_run_capacity": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
     "fq_run_set_tables": (C.c_int, [C.c_void_p, C.c_uint, C.c_uint]),
+    "fq_run_set_spawn_split": (C.c_int, [C.c_void_p, C.c_uint]),
     "fq_run_merge_paths": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "fq_run_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "fq_run_profile": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_float)]),

@@ -90,6 +90,8 @@ struct fq_run {
     const KernelSet* ks;
     int log2B;
     unsigned B, Cv, Cs, slots;  // slots: on-chip table slots per merge warp
+    unsigned Cp;                // spawn slots per bucket in the dense primary region
+    bool no_spawn_buf;          // a failed growth left no spawn buffers: the run cannot step
     RunState* st;
     StatsRow* hist;
     unsigned* vcount[2];
@@ -534,6 +536,7 @@ static void fill_desc(const fq_run* r, RunDesc& d, unsigned seg_base) {
     d.seg_base = seg_base;
     d.Cv = r->Cv;
     d.Cs = r->Cs;
+    d.Cp = r->Cp;
     for (int i = 0; i < 2; ++i) {
         d.vkeys[i] = r->vkeys[i];
         d.vamps[i] = r->vamps[i];
@@ -619,6 +622,16 @@ static void segment_caps(double lcap, double scap, unsigned B, double k, unsigne
     Cs = (unsigned)((ms + 4.0 * std::sqrt(ms * k) + k + 16.0 + 31.0) / 32.0) * 32u;
 }
 
+// Spawn slots per bucket in the dense primary region: the steady-state fill
+// plus three standard deviations of its compound-Poisson count (a multiple
+// of 32, at most the bucket's capacity), so that nearly every spawn of an
+// equilibrated run is stored there.
+static unsigned primary_slots(double s_ss, unsigned B, double k, unsigned Cs) {
+    const double m = s_ss / B;
+    const unsigned p = (unsigned)((m + 3.0 * std::sqrt(m * k) + 16.0 + 31.0) / 32.0) * 32u;
+    return std::min(p, Cs);
+}
+
 static void batch_free(fq_batch* b);
 static int batch_build(fq_batch* b);
 
@@ -688,6 +701,7 @@ extern "C" int fq_run_create(fq_run** out, const fq_ham* h, const fq_params* p, 
         // bucket count fluctuates like a compound Poisson sum with clump size k
         const double k = r->det ? (double)max_offdiag(h->mp) : 8.0;
         segment_caps(lcap, scap, r->B, k, r->Cv, r->Cs);
+        r->Cp = primary_slots(s_ss, r->B, k, r->Cs);
         table_sizes(r);
     }
     r->log2B = ilog2(r->B);
@@ -1360,6 +1374,7 @@ static int single_batch(fq_run* r) {
 extern "C" int fq_run_step(fq_run* r, int64_t n) {
     if (!r || n < 0) return FQ_ERR_INVALID;
     if (!r->seeded) return FQ_ERR_INVALID;
+    if (r->no_spawn_buf) return FQ_ERR_NOMEM;
     int rc = single_batch(r);
     if (rc) return rc;
     return batch_launch(r->single, n);
@@ -1368,6 +1383,7 @@ extern "C" int fq_run_step(fq_run* r, int64_t n) {
 // read the device error; on error roll the run back to its last completed
 // step (the current buffer and state are untouched by a failed step)
 static int run_check(fq_run* r) {
+    if (r->no_spawn_buf) return FQ_ERR_NOMEM;
     CK(cudaStreamSynchronize(r->stream));
     unsigned err = 0;
     CK(cudaMemcpy(&err, &r->st->err, sizeof err, cudaMemcpyDeviceToHost));
@@ -1456,7 +1472,7 @@ static int gather(fq_run* r, const void* keys, const void* vals, unsigned cap, c
     CK(bufs.get(&d_k, kb * T));
     CK(bufs.get(&d_v, sizeof(double) * T));
     CK(cudaMemcpy(d_off, off.data(), sizeof(unsigned) * (B + 1), cudaMemcpyHostToDevice));
-    if (spawns) r->ks->gather_spawns(keys, vals, cap, cnt_dev, d_off, B, d_k, d_v, 0);
+    if (spawns) r->ks->gather_spawns(keys, vals, cap, r->Cp, cnt_dev, d_off, B, d_k, d_v, 0);
     else r->ks->gather_vec(keys, vals, cap, cnt_dev, d_off, B, d_k, d_v, nullptr, 0);
     CK(cudaDeviceSynchronize());
     std::vector<unsigned char> kbuf(kb * T);
@@ -1523,24 +1539,35 @@ extern "C" int fq_run_reserve(fq_run* r, size_t capacity_vec, size_t capacity_sp
         }
         r->Cv = Cv;
     }
+    int out = FQ_OK;
     if (Cs > r->Cs) {
-        void* nk = dev_alloc(r, r->ks->spawn_key_stride * (size_t)r->B * Cs);
-        void* nv = dev_alloc(r, std::max<size_t>(16, r->ks->spawn_val_stride * (size_t)r->B * Cs));
-        if (!nk || !nv) {
-            if (nk) dev_free(r, nk);
-            if (nv) dev_free(r, nv);
-            return FQ_ERR_NOMEM;
-        }
+        // the spawn buffers hold nothing between steps: the old ones are
+        // released first, so growing them needs no room for both
+        auto spawn_alloc = [&](unsigned cs, void** k, void** v) {
+            *k = dev_alloc(r, r->ks->spawn_key_stride * (size_t)r->B * cs);
+            *v = dev_alloc(r, std::max<size_t>(16, r->ks->spawn_val_stride * (size_t)r->B * cs));
+            if (*k && *v) return true;
+            if (*k) dev_free(r, *k);
+            if (*v) dev_free(r, *v);
+            *k = *v = nullptr;
+            return false;
+        };
         dev_free(r, r->skeys);
         dev_free(r, r->samps);
+        void *nk, *nv;
+        if (spawn_alloc(Cs, &nk, &nv)) {
+            r->Cs = Cs;
+        } else {
+            out = FQ_ERR_NOMEM;  // back to the old size, which fitted before
+            if (!spawn_alloc(r->Cs, &nk, &nv)) r->no_spawn_buf = true;
+        }
         r->skeys = nk;
         r->samps = nv;
-        r->Cs = Cs;
     }
     table_sizes(r);
     r->gen++;
     CK(sync_self(r));
-    return FQ_OK;
+    return out;
 }
 
 extern "C" int fq_run_capacity(const fq_run* r, size_t* capacity_vec, size_t* capacity_spawn) {
@@ -1564,6 +1591,17 @@ extern "C" int fq_run_set_tables(fq_run* r, unsigned slots, unsigned scratch_slo
     table_sizes(r);
     r->has_tuned = false;  // a tuned shape was timed with the old tables
     r->gen++;
+    return FQ_OK;
+}
+
+extern "C" int fq_run_set_spawn_split(fq_run* r, unsigned primary) {
+    if (!r) return FQ_ERR_INVALID;
+    int rc = run_check(r);
+    if (rc) return rc;
+    if (primary % 32u || primary > r->Cs) return FQ_ERR_INVALID;
+    r->Cp = primary;
+    r->gen++;
+    CK(sync_self(r));
     return FQ_OK;
 }
 
@@ -1876,6 +1914,8 @@ extern "C" void fq_batch_destroy(fq_batch* b) {
 
 extern "C" int fq_batch_step(fq_batch* b, int64_t n) {
     if (!b) return FQ_ERR_INVALID;
+    for (fq_run* r : b->runs)
+        if (r->no_spawn_buf) return FQ_ERR_NOMEM;
     return batch_launch(b, n);
 }
 

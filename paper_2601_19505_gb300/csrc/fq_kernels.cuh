@@ -59,6 +59,22 @@ template <> struct Var<2> { static constexpr int WPB = 4, MINB = 6; };
 constexpr int kVariants = 3;
 
 // ---------------------------------------------------------------------------
+// Where slot `pos` of bucket b lies in the spawn buffers (B buckets of Cs
+// slots).  The first Cp slots of every bucket form a dense primary region of
+// B Cp entries; the other Cs - Cp slots of every bucket follow it.  Spawns
+// land in random buckets, so each store touches a random page of the region
+// it falls in, and on GB300 such stores slow down with the size of that
+// region (measured: 4.9e8 random 32-byte stores took 27 ms spread over
+// 51 GB, 56 ms over 103 GB).  A primary region sized for the steady-state
+// bucket fill keeps nearly every store in a small region while the
+// capacity for transients stays.
+__host__ __device__ __forceinline__ size_t spawn_slot(unsigned b, unsigned pos, unsigned Cp,
+                                                      unsigned Cs, unsigned B) {
+    return pos < Cp ? (size_t)b * Cp + pos
+                    : (size_t)B * Cp + (size_t)b * (Cs - Cp) + (pos - Cp);
+}
+
+// ---------------------------------------------------------------------------
 // Spawn buffers.  64-bit addresses: a key array and a value array.  128-bit
 // addresses: one 32-byte record per spawn (address, value, zero padding),
 // which fills exactly one 32-byte DRAM sector, so a spawn is stored as a
@@ -66,7 +82,7 @@ constexpr int kVariants = 3;
 // contents to merge a partial write (spawns land in random buckets, so the
 // sectors of separate 16-byte keys and 8-byte values were mostly written
 // partly).  `kb` and `vb` are the run's skeys and samps; entry i of bucket b
-// is at i = b Cs + position.
+// is at spawn_slot(b, i, ...).
 template <class K, class S> struct SpawnIO {
     static constexpr bool REC = sizeof(K) == 16;
     static constexpr size_t key_bytes = REC ? 32 : sizeof(K);  // bytes per entry of kb
@@ -220,7 +236,7 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     const K* vk0 = nullptr;
     const A* va0 = nullptr;
     const unsigned* vcnt = nullptr;
-    unsigned Cv = 0, Cs = 0, stepno = 0;
+    unsigned Cv = 0, Cs = 0, Cp = 0, stepno = 0;
     void* sk = nullptr;
     void* sv = nullptr;
     unsigned* sfill = nullptr;
@@ -243,7 +259,7 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
     auto flush_pending = [&]() {
         if (!ph) return;
         if (pp < Cs) {
-            SpawnIO<K, S>::store(sk, sv, (size_t)pb * Cs + pp, pd, pv);
+            SpawnIO<K, S>::store(sk, sv, spawn_slot(pb, pp, Cp, Cs, run_hi - run_lo), pd, pv);
         } else {
             atomicOr(&R->st->err, FQ_DERR_SPAWN_CAP);
         }
@@ -282,6 +298,7 @@ k_spawn(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
         vcnt = R->vcount[cur];
         Cv = R->Cv;
         Cs = R->Cs;
+        Cp = R->Cp;
         sk = R->skeys;
         sv = R->samps;
         sfill = R->sfill;
@@ -876,7 +893,7 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
     A* __restrict__ oa = (A*)R->vamps[cur ^ 1] + (size_t)seg * Cv;
     const void* const skb = R->skeys;
     const void* const svb = R->samps;
-    const size_t s0 = (size_t)seg * R->Cs;
+    const unsigned sCp = R->Cp, sCs = R->Cs, sB = R->B;
     const unsigned stepno = (unsigned)(R->st->step + 1);
     const uint2 rkey = make_uint2(R->key_x, R->key_y);
     const int nq = R->norm_q;
@@ -891,14 +908,16 @@ __device__ __forceinline__ void merge_bucket(const RunDesc* R, unsigned seg, uns
     {
         K skey = EMPTY;
         S sval = (S)0;
-        if (lane < n_sp) SpawnIO<K, S>::load(skb, svb, s0 + lane, skey, sval);
+        if (lane < n_sp)
+            SpawnIO<K, S>::load(skb, svb, spawn_slot(seg, lane, sCp, sCs, sB), skey, sval);
         for (unsigned j0 = 0; j0 < n_sp; j0 += 32) {
             const unsigned j = j0 + lane;
             bool nw = false;
             int q = -1;
             const K key = skey;
             const S v = sval;
-            if (j + 32 < n_sp) SpawnIO<K, S>::load(skb, svb, s0 + j + 32, skey, sval);
+            if (j + 32 < n_sp)
+                SpawnIO<K, S>::load(skb, svb, spawn_slot(seg, j + 32, sCp, sCs, sB), skey, sval);
             if (j < n_sp) {
                 q = table_insert(tk, mask, key, nw);
                 if (q < 0) acc.full = true;
@@ -1024,7 +1043,7 @@ __device__ __forceinline__ void sort_bucket(const RunDesc* R, unsigned seg, unsi
     const A* __restrict__ va = (const A*)R->vamps[cur] + (size_t)seg * Cv;
     K* __restrict__ ok = (K*)R->vkeys[cur ^ 1] + (size_t)seg * Cv;
     A* __restrict__ oa = (A*)R->vamps[cur ^ 1] + (size_t)seg * Cv;
-    const size_t s0 = (size_t)seg * R->Cs;
+    const unsigned sCp = R->Cp, sCs = R->Cs, sB = R->B;
     const unsigned stepno = (unsigned)(R->st->step + 1);
     const uint2 rkey = make_uint2(R->key_x, R->key_y);
     const int nq = R->norm_q, det = R->mode_det, early = R->early;
@@ -1047,7 +1066,7 @@ __device__ __forceinline__ void sort_bucket(const RunDesc* R, unsigned seg, unsi
     for (unsigned j = lane; j < n_sp; j += 32) {
         K key;
         S sval;
-        SpawnIO<K, S>::load(R->skeys, R->samps, s0 + j, key, sval);
+        SpawnIO<K, S>::load(R->skeys, R->samps, spawn_slot(seg, j, sCp, sCs, sB), key, sval);
         const unsigned i = n_old + j;
         wk[i] = key;
         wv[i] = (ACC)sval;
@@ -1224,20 +1243,33 @@ k_merge(const RunDesc* __restrict__ runs, const unsigned* __restrict__ seg_run, 
             if (lane == 0) {
                 typedef typename AmpT<AMP>::A A;
                 typedef typename AmpT<AMP>::S S;
-                const size_t vo = (size_t)(seg + 1) * R->Cv, so = (size_t)(seg + 1) * R->Cs;
+                const size_t vo = (size_t)(seg + 1) * R->Cv;
                 // capacities are multiples of 32 entries; sizes kept below 2^30
                 const unsigned Cv = min(R->Cv, 1u << 25), Cs = min(R->Cs, 1u << 25);
+                const unsigned Cp = min(R->Cp, Cs);
                 const unsigned po = min(o1, Cv), ps = min(s1, Cs);
                 prefetch_l2((const K*)R->vkeys[cur] + vo, po * (unsigned)sizeof(K),
                             Cv * (unsigned)sizeof(K));
                 prefetch_l2((const A*)R->vamps[cur] + vo, po * (unsigned)sizeof(A),
                             Cv * (unsigned)sizeof(A));
                 typedef SpawnIO<K, S> IO;
-                prefetch_l2((const unsigned char*)R->skeys + so * IO::key_bytes,
-                            ps * (unsigned)IO::key_bytes, Cs * (unsigned)IO::key_bytes);
-                if (IO::val_bytes)
-                    prefetch_l2((const unsigned char*)R->samps + so * IO::val_bytes,
-                                ps * (unsigned)IO::val_bytes, Cs * (unsigned)IO::val_bytes);
+                // the bucket's primary slots, then those beyond them
+                const unsigned p1 = min(ps, Cp), p2 = ps - p1;
+                const size_t so1 = spawn_slot(seg + 1, 0, Cp, Cs, R->B),
+                             so2 = spawn_slot(seg + 1, Cp, Cp, Cs, R->B);
+                prefetch_l2((const unsigned char*)R->skeys + so1 * IO::key_bytes,
+                            p1 * (unsigned)IO::key_bytes, Cp * (unsigned)IO::key_bytes);
+                if (p2)
+                    prefetch_l2((const unsigned char*)R->skeys + so2 * IO::key_bytes,
+                                p2 * (unsigned)IO::key_bytes, (Cs - Cp) * (unsigned)IO::key_bytes);
+                if (IO::val_bytes) {
+                    prefetch_l2((const unsigned char*)R->samps + so1 * IO::val_bytes,
+                                p1 * (unsigned)IO::val_bytes, Cp * (unsigned)IO::val_bytes);
+                    if (p2)
+                        prefetch_l2((const unsigned char*)R->samps + so2 * IO::val_bytes,
+                                    p2 * (unsigned)IO::val_bytes,
+                                    (Cs - Cp) * (unsigned)IO::val_bytes);
+                }
             }
             ahead_g = g + 1;
             a1_old = o1;
@@ -1843,7 +1875,7 @@ __global__ void k_gather(const K* __restrict__ keys, const T* __restrict__ vals,
 // the same for spawn buckets, in their layout
 template <class K, class S>
 __global__ void k_gather_spawns(const void* __restrict__ kb, const void* __restrict__ vb,
-                                unsigned cap, const unsigned* __restrict__ cnt,
+                                unsigned cap, unsigned Cp, const unsigned* __restrict__ cnt,
                                 const unsigned* __restrict__ off, unsigned B, K* __restrict__ okeys,
                                 double* __restrict__ ovals) {
     for (unsigned b = blockIdx.x; b < B; b += gridDim.x) {
@@ -1851,7 +1883,7 @@ __global__ void k_gather_spawns(const void* __restrict__ kb, const void* __restr
         for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
             K key;
             S v;
-            SpawnIO<K, S>::load(kb, vb, (size_t)b * cap + i, key, v);
+            SpawnIO<K, S>::load(kb, vb, spawn_slot(b, i, Cp, cap, B), key, v);
             okeys[o + i] = key;
             ovals[o + i] = (double)v;
         }

@@ -116,10 +116,10 @@ template <class K, int AMP, int KIND> struct Launch {
         if (!n) return;
         k_lookup<K, AMP><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d, (const K*)keys, n, out);
     }
-    static void gather_spawns(const void* keys, const void* vals, unsigned cap, const unsigned* cnt,
-                              const unsigned* off, unsigned B, void* okeys, double* ovals,
-                              cudaStream_t s) {
-        k_gather_spawns<K, S><<<B < 4096 ? B : 4096, 256, 0, s>>>(keys, vals, cap, cnt, off, B,
+    static void gather_spawns(const void* keys, const void* vals, unsigned cap, unsigned Cp,
+                              const unsigned* cnt, const unsigned* off, unsigned B, void* okeys,
+                              double* ovals, cudaStream_t s) {
+        k_gather_spawns<K, S><<<B < 4096 ? B : 4096, 256, 0, s>>>(keys, vals, cap, Cp, cnt, off, B,
                                                                   (K*)okeys, ovals);
     }
     static void column(const ModelParams& mp, const void* key, void* dest, double* val,

@@ -27,8 +27,9 @@ struct KernelSet {
     void (*lookup)(const RunDesc* d, const void* keys, size_t n, double* out, cudaStream_t);
     void (*restride)(const void* ok, const void* oa, unsigned oc, const unsigned* cnt, unsigned B,
                      void* nk, void* na, unsigned nc, cudaStream_t);
-    void (*gather_spawns)(const void* keys, const void* vals, unsigned cap, const unsigned* cnt,
-                          const unsigned* off, unsigned B, void* okeys, double* ovals, cudaStream_t);
+    void (*gather_spawns)(const void* keys, const void* vals, unsigned cap, unsigned Cp,
+                          const unsigned* cnt, const unsigned* off, unsigned B, void* okeys,
+                          double* ovals, cudaStream_t);
     void (*column)(const ModelParams&, const void* key, void* dest, double* val, unsigned cap,
                    double* diag, unsigned* m, cudaStream_t);
     void (*ref_count)(const ModelParams&, const void* refs, int n, unsigned* m, cudaStream_t);

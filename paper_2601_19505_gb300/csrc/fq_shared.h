@@ -93,6 +93,7 @@ struct RunDesc {
     unsigned key_x, key_y;   // Philox key
     int log2B;
     unsigned B, seg_base, Cv, Cs;
+    unsigned Cp;             // spawn slots per bucket in the dense primary region (<= Cs)
     void* vkeys[2];
     void* vamps[2];
     unsigned* vcount[2];

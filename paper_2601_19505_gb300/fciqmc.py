@@ -287,6 +287,10 @@ class Run:
         _check(self._lib.fq_run_set_tables(self.r, int(slots), int(scratch_slots)),
                "fq_run_set_tables")
 
+    def set_spawn_split(self, primary: int):
+        """fq_run_set_spawn_split: spawn slots per bucket in the dense primary region."""
+        _check(self._lib.fq_run_set_spawn_split(self.r, int(primary)), "fq_run_set_spawn_split")
+
     def merge_paths(self):
         """fq_run_merge_paths: (on-chip, scratch) bucket counts since seeding."""
         a, b = C.c_uint64(), C.c_uint64()

@@ -301,3 +301,45 @@ def test_scratch_table_overflow_rolls_back():
     o.step(1)
     assert_same_vector(g.export(), o.export(), rtol=1e-12, what="after the failed step")
     assert g.merge_paths()[1] > 0
+
+
+@pytest.mark.parametrize("primary", [0, 32, 64])
+@pytest.mark.parametrize("mode", ["REAL64", "INT"])
+@pytest.mark.parametrize("model", [MODELS[1], MODELS[3]], ids=["real1d-64bit", "real2d-128bit"])
+def test_spawn_split_matches_oracle(model, mode, primary):
+    """The spawn buffers keep the first `primary` slots of every bucket in a
+    dense region and the rest in a second one.  With a 20k-entry seeded vector
+    the buckets fill past 32 and 64 slots, so spawns land in both regions (0:
+    all in the second); the spawn list and three steps still match the
+    oracle, and an invalid split is rejected.  (A target of an eighth of
+    the seeded norm gives buckets of about 390 to 530 spawns in REAL64 and 34
+    to 130 for integer walkers.)"""
+    h, m = pair(*model)
+    mcode = {"REAL64": 1, "INT": 0}[mode]
+    keys, amps = seeded_vector(m, 20000, 41, mode=mode)
+    g, o = runs(h, m, mode=mcode, dt=0.001, target=float(np.abs(amps).sum()) / 8, seed=7,
+                capacity_vec=200000, capacity_spawn=2000000)
+    g.set_spawn_split(primary)
+    with pytest.raises(fq().FqError):
+        g.set_spawn_split(primary + 16)  # not a multiple of 32
+    g.seed(fq().keys_from_ints(keys), amps, -2.0, step=100)
+    o.seed(keys, amps, -2.0, step=100)
+    o.record_spawns()
+    gd, gv = g.spawns()
+    o.step(1)
+    od, osrc, ov = o.spawns()
+    assert len(gd) == len(od)
+    gd, gv = sorted_pairs(gd, gv)
+    od, ov = sorted_pairs(od, ov)
+    assert np.array_equal(gd["lo"], od["lo"]) and np.array_equal(gd["hi"], od["hi"])
+    assert np.array_equal(gv, ov)
+    rtol = {"REAL64": 1e-12, "INT": 0.0}[mode]
+    g.step(1)
+    assert_same_vector(g.export(), o.export(), rtol=rtol, what="step 0")
+    for s in range(1, 3):
+        g.step(1)
+        o.step(1)
+        assert_same_vector(g.export(), o.export(), rtol=rtol, what="step %d" % s)
+    gh, oh = g.history(), o.history()
+    for f in ("len", "exact_steps", "inexact_steps", "n_spawns"):
+        assert np.array_equal(gh[f], oh[f]), f
