@@ -75,22 +75,24 @@ __host__ __device__ __forceinline__ size_t spawn_slot(unsigned b, unsigned pos, 
 }
 
 // ---------------------------------------------------------------------------
-// Spawn buffers.  64-bit addresses: a key array and a value array.  128-bit
-// addresses: one 32-byte record per spawn (address, value, zero padding),
-// which fills exactly one 32-byte DRAM sector, so a spawn is stored as a
-// whole sector and the memory system never has to read the sector's old
-// contents to merge a partial write (spawns land in random buckets, so the
-// sectors of separate 16-byte keys and 8-byte values were mostly written
-// partly).  `kb` and `vb` are the run's skeys and samps; entry i of bucket b
-// is at spawn_slot(b, i, ...).
+// Spawn buffers: one record per spawn in `kb` (the run's skeys; `vb`, its
+// samps, is unused).  128-bit addresses: 32 bytes (address, value, zero
+// padding), which fill exactly one 32-byte DRAM sector, so a spawn is stored
+// as a whole sector and the memory system never has to read the sector's
+// old contents to merge a partial write (spawns land in random buckets, so
+// the sectors of separate 16-byte keys and 8-byte values were mostly written
+// partly).  64-bit addresses: 16 bytes (address, value).  Entry i of bucket
+// b is at spawn_slot(b, i, ...).
 template <class K, class S> struct SpawnIO {
     static constexpr bool REC = sizeof(K) == 16;
-    static constexpr size_t key_bytes = REC ? 32 : sizeof(K);  // bytes per entry of kb
-    static constexpr size_t val_bytes = REC ? 0 : sizeof(S);   // bytes per entry of vb
-    // A record is written by one 256-bit store: a random-bucket store is one
-    // request to the memory system instead of two (measured on the spawn
-    // kernel's store pattern: 4.9e8 records in 15 ms against 27 ms as two
-    // 16-byte stores).  Records are 32-byte aligned (the buffers are).
+    static constexpr size_t key_bytes = REC ? 32 : 16;  // bytes per entry of kb
+    static constexpr size_t val_bytes = 0;              // bytes per entry of vb
+    // A record is written by one store (256 or 128 bits): a random-bucket
+    // store is one request to the memory system instead of two (measured on
+    // the spawn kernel's store pattern: 4.9e8 32-byte records in 15 ms
+    // against 27 ms as two 16-byte stores; c2's spawn kernel 9 % faster with
+    // 16-byte records than with separate address and value arrays).  Records
+    // are aligned to their size (the buffers are 256-byte aligned).
     __device__ __forceinline__ static void store(void* kb, void* vb, size_t i, K key, S v) {
         if constexpr (REC) {
             unsigned char* p = (unsigned char*)kb + i * 32;
@@ -102,8 +104,12 @@ template <class K, class S> struct SpawnIO {
                          "l"(vbits), "l"(0ull)
                          : "memory");
         } else {
-            ((K*)kb)[i] = key;
-            ((S*)vb)[i] = v;
+            unsigned long long vbits = 0;
+            memcpy(&vbits, &v, sizeof(S));
+            unsigned char* p = (unsigned char*)kb + i * 16;
+            asm volatile("st.global.v2.b64 [%0], {%1, %2};\n" ::"l"(p), "l"((unsigned long long)key),
+                         "l"(vbits)
+                         : "memory");
         }
     }
     __device__ __forceinline__ static void load(const void* kb, const void* vb, size_t i, K& key,
@@ -118,8 +124,11 @@ template <class K, class S> struct SpawnIO {
             key = (K)lo | ((K)hi << 32 << 32);
             memcpy(&v, &vbits, sizeof(S));
         } else {
-            key = ((const K*)kb)[i];
-            v = ((const S*)vb)[i];
+            const unsigned char* p = (const unsigned char*)kb + i * 16;
+            unsigned long long kk, vbits;
+            asm volatile("ld.global.v2.b64 {%0, %1}, [%2];\n" : "=l"(kk), "=l"(vbits) : "l"(p));
+            key = (K)kk;
+            memcpy(&v, &vbits, sizeof(S));
         }
     }
 };
