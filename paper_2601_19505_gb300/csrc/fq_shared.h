@@ -1,4 +1,4 @@
-// fq_shared.h -- plain structs shared by the host driver (fq_api.cu) and the
+// fq_shared.h -- plain structs shared by the host code (fq_api.cu) and the
 // kernels: model parameters, per-run device state, the per-run descriptor
 // the batched kernels read, and launch shapes.
 #pragma once

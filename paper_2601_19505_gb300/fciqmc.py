@@ -358,7 +358,7 @@ class Run:
             if rc == -3 and grows < max_grows:
                 v, s = self.capacity()
                 if self._alloc is not None:
-                    # hand cached blocks back to the driver before the copy
+                    # hand cached blocks back to the CUDA driver before the copy
                     self._alloc.torch.cuda.empty_cache()
                 self.reserve(int(v * grow), int(s * grow))
                 grows += 1

@@ -171,7 +171,7 @@ def test_ed_12x12_as_printed():
     e = ED.lowest(m, 2)
     assert np.allclose(e, g["ed_12x12_u6"], atol=g["ed_tol"])
     # Sec. 2.3: the on-site correlation <G2(0)> of this ground state is
-    # "around 20%"; G2(0) is diagonal, (1/M) sum_i n_i (n_i - 1) (Eq. g2)
+    # about one fifth (Sec. 2.3); G2(0) is diagonal, (1/M) sum_i n_i (n_i - 1) (Eq. g2)
     go = golden("observables.json")
     e0, basis, v0 = ED.ground_state(m)
     g20 = np.array([m.g2_diag(b, 0) for b in ED.basis_ints(basis)])
