@@ -57,7 +57,9 @@ DTYPE = {"INT": "int64", "REAL64": "f64", "REAL32": "f32", "DETERMINISTIC": "f64
 ANN_CODE = {"auto": 0, "sort": 1, "hash": 2}
 # bytes fq_run_stats copies back per call: the error word and the run state
 STATS_D2H_BYTES = 4 + 192  # the error word, then the 192-byte run state
-KERNEL_FILES = ["fq_kernels.cuh", "fq_device.cuh", "fq_shared.h"]
+# the sources a committed ncu summary depends on: the kernels, and the host
+# code that sizes the buffers, tables and launch shapes they run with
+KERNEL_FILES = ["fq_kernels.cuh", "fq_device.cuh", "fq_shared.h", "fq_launch.cuh", "fq_api.cu"]
 
 
 def describe(cfg, name):

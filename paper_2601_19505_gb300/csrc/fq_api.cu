@@ -592,10 +592,16 @@ static LaunchCfg make_cfg(const KernelSet* ks, int spawn_var, int spawn_waves, i
 }
 
 // on-chip table slots per merge warp: 512, fewer if a warp's share of
-// shared memory would not allow two 8-warp blocks per SM
+// shared memory would not allow two 8-warp blocks per SM (2 x (112 KB +
+// the 1 KB the SM reserves per block) within its 228 KB).  The bucket count
+// follows (a bucket's spawns fill about a third of the table), so the
+// larger table also means fewer, fuller buckets: on the 127-bit c5
+// workload 512 slots and 2^22 buckets stepped 12 % faster than 256 slots
+// and 2^23 buckets (fewer per-bucket costs in the merge; fewer counters
+// and a denser primary region for the spawn stores).
 static unsigned warp_slots(const KernelSet* ks) {
     unsigned sw = 512;
-    while (sw > 128 && 8ull * sw * ks->slot_bytes > 110u * 1024u) sw >>= 1;
+    while (sw > 128 && 8ull * sw * ks->slot_bytes > 112u * 1024u) sw >>= 1;
     return sw;
 }
 
