@@ -707,6 +707,81 @@ def c3_trajectory_arm(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Late against early compression and the semistochastic threshold t_rel
+# (Sec. 7, Eq. early-comp): the statistical efficiency of the shift,
+# f = 1 / (sigma_S^2 Omega t~) with the blocked error sigma_S of its mean,
+# Omega timed steps and t~ the median time of a step (here CUDA-event time
+# on the GPU), on the model families of the paper's two comparisons: real
+# space M = N = 12, u = 6 (t_rel and the compression style), and momentum
+# space M = N = 10, u = 6 (the compression style against N_t, where the
+# sign problem shows).  The exact-column rule is |c| t_rel >= m (reading of
+# Sec. 7.1), so a smaller t_rel takes fewer exact columns.
+
+def compression_sweep_arm(args):
+    import torch
+
+    import paper_2601_19505_gb300 as fq
+    from paper_2601_19505_gb300 import analysis as A
+
+    steps = max(1000, int(args.sweep_steps))
+    chunk = 1000
+    equil = steps // 10
+    out = {"steps": steps, "equilibration_steps": equil, "chunk": chunk, "dt": 1e-3,
+           "real_space": [], "momentum_space": []}
+
+    def one(kind, M, N, u, target, compression, t_rel, seed=1):
+        h = fq.Hamiltonian(kind, M, 1, N, 1.0, u)
+        p = fq.default_params(mode=MODE_CODE["REAL64"], dt=1e-3, target=float(target), seed=seed,
+                              compression=compression, t_rel=float(t_rel))
+        run = fq.Run(h, p)
+        run.seed_default(W.START_WEIGHT)
+        run.advance(equil, chunk=min(equil, 5000))
+        run.history()  # drain the equilibration rows
+        stream = torch.cuda.ExternalStream(run.stream) if run.stream else torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        times, rows = [], []
+        for _ in range(steps // chunk):
+            torch.cuda.synchronize()
+            e0.record(stream)
+            run.advance(chunk, chunk=chunk)  # grows the capacities if a step overflows them
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3 / chunk)
+            rows.append(run.history())
+        hist = np.concatenate(rows)
+        run.close()
+        sh = A.blocked_mean(hist["shift"])
+        e = A.ratio_estimate(hist["hproj"], hist["vproj"])
+        t_med = float(np.median(times))
+        ex = hist["exact_steps"].astype(float)
+        tot = ex + hist["inexact_steps"].astype(float)
+        return {"compression": "early" if compression else "late", "t_rel": t_rel,
+                "target": target, "steps": int(len(hist)),
+                "shift_mean": sh["mean"], "shift_err": sh["err"],
+                "projected": e["ratio"], "projected_err": e["err"],
+                "t_step_us": 1e6 * t_med,
+                "f_shift": 1.0 / (sh["err"] ** 2 * len(hist) * t_med) if sh["err"] > 0 else None,
+                "len_mean": float(hist["len"].mean()), "spawns_mean": float(hist["n_spawns"].mean()),
+                "exact_fraction": float(np.mean(ex / np.maximum(tot, 1.0)))}
+
+    def safe(*a):
+        try:
+            return one(*a)
+        except fq.FqError as e:  # a population that dies or outgrows the device
+            return {"compression": "early" if a[5] else "late", "t_rel": a[6], "target": a[4],
+                    "error": str(e)}
+
+    for comp in (0, 1):
+        for t_rel in (1e-9, 1.0 / 16, 0.25, 1.0, 4.0, 16.0, 64.0, 256.0):
+            out["real_space"].append(safe(1, 12, 12, 6.0, 1e4, comp, t_rel))
+        for target in (30, 100, 300, 1000, 3000, 10000):
+            out["momentum_space"].append(safe(3, 10, 10, 6.0, target, comp, 1.0))
+    print(json.dumps({"metric": "statistical efficiency of the shift (compression styles, t_rel)",
+                      "compression_sweep": out}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -736,6 +811,12 @@ def main():
     ap.add_argument("--c3-trajectory", action="store_true",
                     help="c3: FP32 against FP64 trajectories over 5000 steps at N_t = 1e6 and "
                          "1e7, and the first --steps steps at the configuration's N_t")
+    ap.add_argument("--compression-sweep", action="store_true",
+                    help="late against early compression and the semistochastic threshold: "
+                         "statistical efficiency of the shift on 12/12 real space and 10/10 "
+                         "momentum space")
+    ap.add_argument("--sweep-steps", type=int, default=100000,
+                    help="timed steps per run of --compression-sweep")
     ap.add_argument("--mode", choices=sorted(MODE_CODE), default=None,
                     help="the amplitude mode (default: FP64 for the c5 headline, else the "
                          "workload's own)")
@@ -767,6 +848,8 @@ def main():
         return c3_precision_arm(args)
     if args.c3_trajectory:
         return c3_trajectory_arm(args)
+    if args.compression_sweep:
+        return compression_sweep_arm(args)
     dist = Dist(world, "nccl")
     out = gpu_arm(args, cfg, args.config, dist)
     if out is not None and world == 1 and headline and not args.no_more:
