@@ -782,6 +782,117 @@ def compression_sweep_arm(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# The step's variants at c2 size (1D M = N = 20, u = 2, FP64, N_t = 1e7 per
+# run): what replica overlaps (Sec. 4.3), Gram-Schmidt excited states (Sec.
+# 2.2) and early compression (Sec. 7.1) cost per step, with the added
+# kernels' algorithmic bytes over their added time against the HBM peak
+
+def variants_arm(args):
+    import torch
+
+    import paper_2601_19505_gb300 as fq
+
+    cfg = dict(W.CONFIGS["c2"])
+    equil, n = 2500, max(50, min(int(args.steps), 1000))
+    peak, peak_kind = measured_peak()
+    kb, ab, _ = sizes(cfg)
+    out = {"workload": describe(cfg, "c2") + " per run", "timed_steps": n,
+           "equilibration_steps": equil, "peak_gbs": peak, "peak_source": peak_kind}
+
+    def make(run_id, compression=0, keys=None):
+        h = fq.Hamiltonian(cfg["kind"], cfg["Lx"], cfg["Ly"], cfg["N"], cfg["t"], cfg["u"])
+        p = fq.default_params(mode=MODE_CODE["REAL64"], dt=cfg["dt"], target=cfg["target"],
+                              seed=cfg["seed"], run_id=run_id, compression=compression)
+        r = fq.Run(h, p)
+        if keys is None:
+            r.seed_default(W.START_WEIGHT)
+        else:
+            r.seed(fq.keys_from_ints(keys), [W.START_WEIGHT] * len(keys), h.column(keys[0])[0], 0)
+        return h, r
+
+    def per_step(step, stream_handle):
+        stream = torch.cuda.ExternalStream(stream_handle) if stream_handle \
+            else torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        step(n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    # replicas: two runs of one seed (run ids 0 and 1), overlaps off, dot
+    # products only, and dot products with G2(d), d = 0..3
+    (h0, r0), (h1, r1) = make(0), make(1)
+    b = fq.Batch([r0, r1])
+    b.step(equil)
+    b.sync()
+    b.autotune(2)
+    t_base = per_step(b.step, r0.stream)
+    b.set_overlaps([])
+    t_dot = per_step(b.step, r0.stream)
+    b.set_overlaps([0, 1, 2, 3])
+    t_g2 = per_step(b.step, r0.stream)
+    b.sync()
+    L = float(r0.stats()["len"] + r1.stats()["len"])
+    byt = L * (kb + ab)  # both vectors read once per step
+    out["replicas"] = {
+        "ms_per_step_two_runs": t_base, "ms_per_step_with_dots": t_dot,
+        "ms_per_step_with_dots_and_g2_d0_3": t_g2, "len_both_runs": L,
+        "overlap_bytes_per_step": byt,
+        "overlap_gbs_dots": byt / ((t_dot - t_base) * 1e-3) / 1e9 if t_dot > t_base else None,
+        "overlap_gbs_g2": byt / ((t_g2 - t_base) * 1e-3) / 1e9 if t_g2 > t_base else None}
+    b.close()
+    for r in (r0, r1):
+        r.close()
+    release_device_memory()
+
+    # excited states: state 1 also starts on a neighbour of the start address
+    h0, r0 = make(0)
+    start = int(fq.keys_to_ints(r0.export()[0])[0])
+    nb = h0.column(start)[1][0]
+    _, r1 = make(0, keys=[start, nb])
+    b = fq.Batch([r0, r1])
+    b.set_spectral(2)
+    b.step(equil)
+    b.sync()
+    t_gs = per_step(b.step, r0.stream)
+    b.sync()
+    L0, L1 = float(r0.stats()["len"]), float(r1.stats()["len"])
+    b.set_spectral(0)
+    t_plain = per_step(b.step, r0.stream)
+    b.sync()
+    # dots read both vectors, the update reads both and writes state 1 again
+    gbyt = (2.0 * (L0 + L1) + L1) * (kb + ab)
+    out["spectral_K2"] = {
+        "ms_per_step_two_runs": t_plain, "ms_per_step_with_gram_schmidt": t_gs,
+        "len_states": [L0, L1], "gram_schmidt_bytes_per_step": gbyt,
+        "gram_schmidt_gbs": gbyt / ((t_gs - t_plain) * 1e-3) / 1e9 if t_gs > t_plain else None}
+    b.close()
+    for r in (r0, r1):
+        r.close()
+    release_device_memory()
+
+    # early against late compression: one run each, kernel by kernel
+    for comp, name in ((0, "late"), (1, "early")):
+        _, r = make(0, compression=comp)
+        r.advance(equil, chunk=equil)
+        r.history()
+        ms = r.profile(n)
+        hist = r.history()
+        out["compression_" + name] = {
+            "kernel_ms": {"spawn": ms[0], "merge": ms[1], "shift": ms[2]},
+            "ms_per_step": sum(ms), "len_mean": float(hist["len"].mean()),
+            "spawns_mean": float(hist["n_spawns"].mean()),
+            "configs_per_s": float(hist["len"].mean()) / (sum(ms) * 1e-3)}
+        r.close()
+        release_device_memory()
+    print(json.dumps({"metric": METRIC + " (step variants at c2 size)", "variants": out}),
+          flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -815,6 +926,9 @@ def main():
                     help="late against early compression and the semistochastic threshold: "
                          "statistical efficiency of the shift on 12/12 real space and 10/10 "
                          "momentum space")
+    ap.add_argument("--variants", action="store_true",
+                    help="cost per step of replica overlaps, Gram-Schmidt excited states and "
+                         "early compression at c2 size")
     ap.add_argument("--sweep-steps", type=int, default=100000,
                     help="timed steps per run of --compression-sweep")
     ap.add_argument("--mode", choices=sorted(MODE_CODE), default=None,
@@ -850,6 +964,8 @@ def main():
         return c3_trajectory_arm(args)
     if args.compression_sweep:
         return compression_sweep_arm(args)
+    if args.variants:
+        return variants_arm(args)
     dist = Dist(world, "nccl")
     out = gpu_arm(args, cfg, args.config, dist)
     if out is not None and world == 1 and headline and not args.no_more:

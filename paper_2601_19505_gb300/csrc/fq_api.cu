@@ -1078,13 +1078,20 @@ static void overlaps_free(fq_batch* b) {
     b->ov_on = false;
 }
 
+// blocks per SM for a join kernel with `smem` bytes of tables per block:
+// as many as the SM's 228 KB hold (1 KB of it reserved per block), at most 8
+static unsigned long long join_blocks_per_sm(size_t smem) {
+    return std::max<size_t>(1, std::min<size_t>(8, (228u * 1024u) / (smem + 1024u)));
+}
+
 // the overlap launch for the batch's current sizes: one table per warp with
-// at least twice the slots of the largest segment capacity
+// more slots than the largest segment capacity, so an insert always finds
+// one (a segment's typical fill keeps the load near a third)
 static int overlaps_build(fq_batch* b) {
     if (!b->ov_on) return FQ_OK;
     unsigned cv = 0;
     for (fq_run* r : b->runs) cv = std::max(cv, r->Cv);
-    const unsigned T = std::max(64u, next_pow2(2ull * cv));
+    const unsigned T = std::max(64u, next_pow2(cv + 1ull));
     const size_t slot = b->ks->overlap_slot_bytes;
     int wpb = 4;
     while (wpb > 1 && (size_t)wpb * T * slot > 200u * 1024u) wpb >>= 1;
@@ -1095,7 +1102,7 @@ static int overlaps_build(fq_batch* b) {
     const unsigned long long items = (unsigned long long)P * b->runs[0]->B;
     b->ov_wpb = wpb;
     b->ov_grid = (int)std::max<unsigned long long>(
-        1, std::min<unsigned long long>((unsigned long long)num_sms() * (8 / wpb),
+        1, std::min<unsigned long long>((unsigned long long)num_sms() * join_blocks_per_sm(smem),
                                         (items + wpb - 1) / wpb));
     b->ov_table = T;
     const size_t need = (size_t)b->ov_grid * wpb * P * (1 + b->ov_nq);
@@ -1139,12 +1146,12 @@ static void gs_free(fq_batch* b) {
 }
 
 // the Gram-Schmidt launches for the batch's current sizes: one table per
-// warp with at least twice the slots of K segments' entries
+// warp with more slots than K segments' capacities (an insert always finds one)
 static int gs_build(fq_batch* b) {
     if (b->gs_K < 2) return FQ_OK;
     unsigned cv = 0;
     for (int k = 0; k < b->gs_K; ++k) cv = std::max(cv, b->runs[k]->Cv);
-    const unsigned T = std::max(64u, next_pow2(2ull * b->gs_K * cv));
+    const unsigned T = std::max(64u, next_pow2((unsigned long long)b->gs_K * cv + 1ull));
     const size_t slot = b->ks->gs_slot_bytes;
     if ((size_t)T * slot > 200u * 1024u) return FQ_ERR_INVALID;  // segments too large
     int wpb = 4;
@@ -1153,8 +1160,9 @@ static int gs_build(fq_batch* b) {
     const unsigned B = b->runs[0]->B;
     b->gs_wpb = wpb;
     b->gs_grid = (int)std::max<unsigned long long>(
-        1, std::min<unsigned long long>((unsigned long long)num_sms() * (8 / wpb),
-                                        ((unsigned long long)B + wpb - 1) / wpb));
+        1, std::min<unsigned long long>(
+               (unsigned long long)num_sms() * join_blocks_per_sm((size_t)wpb * T * slot),
+               ((unsigned long long)B + wpb - 1) / wpb));
     b->gs_table = T;
     const size_t need = (size_t)b->gs_grid * wpb * 2 * FQ_MAX_SPECTRAL;
     if (need > b->gs_part_n) {

@@ -1527,8 +1527,8 @@ __global__ void __launch_bounds__(128) k_overlap(const RunDesc* __restrict__ run
         const A* aa = (const A*)RA->vamps[ca] + (size_t)seg * RA->Cv;
         const K* kb = (const K*)RB->vkeys[cb] + (size_t)seg * RB->Cv;
         const A* ab = (const A*)RB->vamps[cb] + (size_t)seg * RB->Cv;
-        // A's entries (distinct addresses; the table has at least twice the
-        // slots, so an insert always finds one)
+        // A's entries (distinct addresses; the table has more slots than a
+        // segment's capacity, so an insert always finds one)
         unsigned nl = 0;
         for (unsigned j0 = 0; j0 < na; j0 += 32) {
             const unsigned j = j0 + lane;
