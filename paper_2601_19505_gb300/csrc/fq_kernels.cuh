@@ -184,6 +184,18 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes, unsig
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// L2 prefetch of segment `seg` of vector buffer `buf` of run R: its stored
+// entries' addresses and amplitudes (segments start 16-byte aligned: the
+// capacity Cv is a multiple of 32 entries)
+template <class K, class A>
+__device__ __forceinline__ void prefetch_segment(const RunDesc* R, int buf, unsigned seg) {
+    const unsigned Cv = min(R->Cv, 1u << 25);
+    const unsigned n = min(R->vcount[buf][seg], Cv);
+    const size_t o = (size_t)seg * R->Cv;
+    prefetch_l2((const K*)R->vkeys[buf] + o, n * (unsigned)sizeof(K), Cv * (unsigned)sizeof(K));
+    prefetch_l2((const A*)R->vamps[buf] + o, n * (unsigned)sizeof(A), Cv * (unsigned)sizeof(A));
+}
+
 // a warp copies `bytes` from global (16-byte aligned) to shared
 __device__ __forceinline__ void warp_copy_async(void* dst, const void* src, unsigned bytes, int lane) {
     for (unsigned o = (unsigned)lane * 16u; o < bytes; o += 32u * 16u)
@@ -1522,6 +1534,11 @@ __global__ void __launch_bounds__(128) k_overlap(const RunDesc* __restrict__ run
         }
         const unsigned na = min(RA->vcount[ca][seg], RA->Cv);
         const unsigned nb = min(RB->vcount[cb][seg], RB->Cv);
+        // the next segment of the pair into L2 while this one is joined
+        if (lane == 0 && it + 1 < i1 && seg + 1 < B) {
+            prefetch_segment<K, A>(RA, ca, seg + 1);
+            prefetch_segment<K, A>(RB, cb, seg + 1);
+        }
         if (!na || !nb) continue;
         const K* ka = (const K*)RA->vkeys[ca] + (size_t)seg * RA->Cv;
         const A* aa = (const A*)RA->vamps[ca] + (size_t)seg * RA->Cv;
@@ -1631,6 +1648,10 @@ __global__ void __launch_bounds__(128) k_gs_dots(const RunDesc* __restrict__ run
     unsigned g0, g1;
     warp_range(gs->B, gw, nw, g0, g1);
     for (unsigned seg = g0; seg < g1; ++seg) {
+        if (lane == 0 && seg + 1 < g1) {  // the next segment of every state into L2
+            prefetch_segment<K, A>(Rk, ck, seg + 1);
+            for (int j = 0; j < k; ++j) prefetch_segment<K, A>(runs + j, runs[j].st->cur ^ 1, seg + 1);
+        }
         const unsigned nk = min(Rk->vcount[ck][seg], Rk->Cv);
         const K* kk = (const K*)Rk->vkeys[ck] + (size_t)seg * Rk->Cv;
         const A* ka = (const A*)Rk->vamps[ck] + (size_t)seg * Rk->Cv;
@@ -1733,6 +1754,10 @@ __global__ void __launch_bounds__(128) k_gs_axpy(const RunDesc* __restrict__ run
     unsigned g0, g1;
     warp_range(gs->B, gw, nw, g0, g1);
     for (unsigned seg = g0; seg < g1; ++seg) {
+        if (lane == 0 && seg + 1 < g1) {  // the next segment of every state into L2
+            prefetch_segment<K, A>(R, ck, seg + 1);
+            for (int j = 0; j < k; ++j) prefetch_segment<K, A>(runs + j, runs[j].st->cur ^ 1, seg + 1);
+        }
         const unsigned nk = min(R->vcount[ck][seg], Cv);
         K* const kk = (K*)R->vkeys[ck] + (size_t)seg * Cv;
         A* const ka = (A*)R->vamps[ck] + (size_t)seg * Cv;
